@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: CG time-to-1e-10 and Dslash bandwidth at 32^3 x 64.
+
+Workload (synthetic, seeded): a 32^3 x 64 SU(3) lattice with links
+U = exp(iA), A traceless Hermitian with N(0, 0.25^2) entries (seed 2),
+kappa = 0.156, antiperiodic time, a complex Gaussian source; M^dag M x = phi
+is solved from x0 = 0 to an FP64 true relative residual of 1e-10.
+
+One step = one mixed-precision solve (inner precision --inner, FP64
+reliable updates every 50 iterations).  Printed as one JSON line:
+  value         solves per second over all ranks (device-timed, data resident)
+  e2e           the same through the C interface with pinned host buffers
+                (gauge field and source copied in, solution copied out, every step)
+  roofline      the Dslash of the inner precision, timed with CUDA events on
+                the library's stream, against the measured HBM copy bandwidth
+  fp64          the plain FP64 CG on the same source (the comparison of the metric)
+  cpu_baseline  the FP64 CPU oracle on a bounded sample, scaled to solves/s
+
+--impl reference times the oracle instead (the CPU program of this project
+written from the paper), on a bounded sample per step.
+Multi-GPU runs (torchrun) are independent replicas: every rank solves its
+own lattice; the time is the maximum over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CG time-to-1e-10 & Dslash GB/s vs HBM peak at 32^3x64, mixed vs FP64"
+DIMS = (32, 32, 32, 64)
+SIGMA, SEED, KAPPA, TOL, RELIABLE = 0.25, 2, 0.156, 1e-10, 50
+WORKLOAD = "cg_32x32x32x64"
+
+# Algorithmic (DRAM-minimal) bytes per site of one application of M: every
+# link and spinor moved once (gauge + input spinor + output spinor).
+DSLASH_BYTES = {"f64": 960, "f32": 480, "f32_12": 384, "f16_12": 200, "bf16_12": 200}
+DSLASH_FLOPS = 1368
+# DRAM traffic per site of the plain Dslash from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum over sites), valid for the kernel sources with this
+# hash; see profiles/.  Null when the kernel changed since the capture.
+NCU_TRAFFIC = {
+    # profiles/dslash_f32_12_32x32x32x32.md: 314.72 MB read + 82.42 MB written over 32^4 sites
+    "f32_12": {"bytes_per_site": 378.7, "src": "e3579385ca518247"},
+    # profiles/dslash_f16_12_32x32x32x32.md: 159.42 MB read + 37.24 MB written over 32^4 sites
+    "f16_12": {"bytes_per_site": 187.6, "src": "e3579385ca518247"},
+}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("lq_device.cuh", "lq_dslash.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1207_2223_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        rows = [ln.split(",") for ln in open(self.f.name).read().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) > 8 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 8 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) > 8 for i in range(4) if r[5 + i].strip() == "Active"})
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def make_inputs():
+    from synth import Lattice, gauge_exp_iA, source
+    lat = Lattice(DIMS)
+    return lat, gauge_exp_iA(lat, SIGMA, SEED), source(lat, SEED)
+
+
+def oracle_cg_iteration_seconds(U, phi, site_fraction=1):
+    """Time the oracle's work for one CG iteration (M^dag M plus the vector updates).
+
+    With site_fraction f > 1, M and M^dag are evaluated on a 1/f sample of the
+    sites (same operator code, gathered) and the time is scaled by f."""
+    import numpy as np
+    from oracle.conventions import neighbours
+    from oracle.wilson import apply_M
+    nbr = neighbours(DIMS, True)
+    V = U.shape[0]
+    sites = None if site_fraction == 1 else np.arange(0, V, site_fraction)
+    t0 = time.perf_counter()
+    a = apply_M(U, phi, DIMS, KAPPA, True, False, sites, nbr)
+    b = apply_M(U, phi, DIMS, KAPPA, True, True, sites, nbr)
+    t1 = time.perf_counter()
+    x = phi.copy()
+    r = phi.copy()
+    alpha = 0.5
+    x = x + alpha * phi
+    r = r - alpha * phi
+    rr = np.vdot(r, r).real
+    p = r + (rr / (rr + 1.0)) * phi
+    t2 = time.perf_counter()
+    del a, b, x, r, p
+    return (t1 - t0) * site_fraction + (t2 - t1)
+
+
+def run_reference(args):
+    import numpy as np
+    rank, size = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    lat, U, phi = make_inputs()
+    n_iter = args.cg_iterations
+    frac = args.ref_site_fraction
+    for _ in range(args.warmup):
+        oracle_cg_iteration_seconds(U, phi, frac)
+    t = [oracle_cg_iteration_seconds(U, phi, frac) for _ in range(args.steps)]
+    per_solve = float(np.mean(t)) * n_iter
+    value = 1.0 / per_solve
+    sample = ("one CG iteration of the FP64 oracle (M and M^dag on every %d-th site, scaled by %d, plus "
+              "the vector updates on the full lattice) per step, times %d iterations (the FP64 CG "
+              "iteration count of this workload)" % (frac, frac, n_iter))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": size,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3 / n_iter,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "dims": list(DIMS), "kappa": KAPPA,
+                                            "sigma": SIGMA, "seed": SEED, "tol": TOL},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_dslash_only(args):
+    """Profiling target: a few applications of M in one precision (no timing output)."""
+    import torch
+    import paper_1207_2223_gb300 as lq
+    from synth import Lattice, gauge_exp_iA, source
+    dims = tuple(args.dims)
+    lat = Lattice(dims)
+    U, phi = gauge_exp_iA(lat, SIGMA, SEED), source(lat, SEED)
+    ctx = lq.lq_create(dims)
+    lq.lq_gauge_set(ctx, torch.from_numpy(U).cuda())
+    ms = lq.lq_time_dslash(ctx, torch.from_numpy(phi).cuda(), KAPPA, False, lq.PRECISIONS[args.dslash_only],
+                           args.steps, False)
+    lq.lq_destroy(ctx)
+    print("dslash %s %s: %.4f ms" % (args.dslash_only, dims, ms))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_1207_2223_gb300 as lq
+    from paper_1207_2223_gb300 import replicas
+
+    rank, size, local = replicas.world()
+    torch.cuda.set_device(local)
+    replicas.init("nccl")
+    dev = torch.device("cuda", local)
+    inner = lq.PRECISIONS[args.inner]
+    lat, U, phi = make_inputs()
+    V = lat.V
+    stream = torch.cuda.current_stream(dev)
+    ctx = lq.lq_create(DIMS, True, stream.cuda_stream)
+    try:
+        Ud = torch.from_numpy(U).to(dev)
+        lq.lq_gauge_set(ctx, Ud)
+        phid = torch.from_numpy(phi).to(dev)
+        x = torch.zeros_like(phid)
+
+        def solve(prec, xo=x, ph=phid):
+            status, st = lq.lq_solve_MdagM(ctx, xo, ph, KAPPA, TOL, 100000, prec, RELIABLE)
+            if status != lq.LQ_OK or st["true_rel_resid"] > TOL:
+                raise RuntimeError("solve failed: status %d %s" % (status, st))
+            return st
+
+        for _ in range(args.warmup):
+            solve(inner)
+        torch.cuda.synchronize(dev)
+        replicas.barrier()
+        clocks = Clocks(local)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        e0.record(stream)
+        for _ in range(args.steps):
+            stats.append(solve(inner))
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop()
+        replicas.barrier()
+        t_local = e0.elapsed_time(e1) / 1e3
+        t_job, units = replicas.combine(t_local, args.steps, dev)
+        value = units / t_job
+        launches = int(sum(s["kernel_launches"] for s in stats))
+
+        # plain FP64 CG on the same source: the comparison of the metric
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        st64 = solve(lq.LQ_F64)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        fp64_s = t0.elapsed_time(t1) / 1e3
+
+        # the dominant kernel, timed alone with CUDA events on the library's stream
+        peaks, peak_kind = load_peaks()
+        hbm = float(peaks["hbm_gbs"])
+        dsl = {}
+        for name in ("f64", "f32", "f32_12", "f16_12", "bf16_12"):
+            ms = lq.lq_time_dslash(ctx, phid, KAPPA, False, lq.PRECISIONS[name], 20, False)
+            gbs = DSLASH_BYTES[name] * V / (ms * 1e-3) / 1e9
+            dsl[name] = {"ms": round(ms, 5), "GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4),
+                         "GFLOP/s": round(DSLASH_FLOPS * V / (ms * 1e-3) / 1e9, 1)}
+        src_hash = kernel_source_hash()
+        tr = NCU_TRAFFIC.get(args.inner)
+        traffic = tr["bytes_per_site"] * V if tr and tr.get("src") == src_hash else None
+        d = dsl[args.inner]
+        roofline = {"kernel": "dslash_kernel<%s> (M, store epilogue)" % args.inner, "bound": "hbm",
+                    "achieved": d["GB/s"], "peak": hbm, "unit": "GB/s", "frac": d["frac_hbm"],
+                    "traffic": traffic, "peak_kind": peak_kind,
+                    "bytes_per_site": DSLASH_BYTES[args.inner], "sites_per_launch": V}
+
+        # end to end through the C interface with pinned host buffers
+        Uh = torch.from_numpy(U).pin_memory()
+        phih = torch.from_numpy(phi).pin_memory()
+        xh = torch.empty_like(phih).pin_memory()
+        lq.lq_gauge_set(ctx, Uh)
+        solve(inner, xh, phih)
+        t_e = time.perf_counter()
+        for _ in range(args.steps):
+            lq.lq_gauge_set(ctx, Uh)
+            solve(inner, xh, phih)
+        e2e_local = time.perf_counter() - t_e
+        e2e_t, e2e_units = replicas.combine(e2e_local, args.steps, dev)
+        e2e = {"value": e2e_units / e2e_t, "unit": "solves/s", "h2d_bytes_per_step": int(U.nbytes + phi.nbytes),
+               "d2h_bytes_per_step": int(phi.nbytes)}
+
+        cpu = None
+        if rank == 0 and size == 1 and not args.no_cpu:
+            t_it = oracle_cg_iteration_seconds(U, phi, args.ref_site_fraction)
+            n_it = st64["iterations"]
+            cpu = {"value": 1.0 / (t_it * n_it), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                   "sample": "one CG iteration of the FP64 oracle (M and M^dag on every %d-th site, scaled, "
+                             "plus the vector updates), times the %d iterations of the FP64 CG"
+                             % (args.ref_site_fraction, n_it),
+                   "seconds_per_iteration": t_it}
+    finally:
+        lq.lq_destroy(ctx)
+
+    mixed_s = t_local / args.steps
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": size, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_job / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if inner != lq.LQ_F64 else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dims": list(DIMS), "kappa": KAPPA, "sigma": SIGMA, "seed": SEED,
+                       "tol": TOL, "inner": args.inner, "reliable_every": RELIABLE,
+                       "l2": "working set larger than L2 (gauge %d MB + spinors), no flush"
+                             % (DSLASH_BYTES[args.inner] * V // 3 // 2**20),
+                       "parallelism": "replicas" if size > 1 else "single"},
+            "time_to_solution_s": {"mixed": mixed_s, "fp64": fp64_s, "speedup": fp64_s / mixed_s},
+            "iterations": {"mixed": stats[-1]["iterations"], "reliable_updates": stats[-1]["reliable_updates"],
+                           "fp64": st64["iterations"]},
+            "true_rel_resid": {"mixed": stats[-1]["true_rel_resid"], "fp64": st64["true_rel_resid"]},
+            "roofline": roofline, "dslash": dsl, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--inner", default="f32_12", choices=["f32", "f32_12", "f16_12", "bf16_12"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--ref-site-fraction", type=int, default=8)
+    ap.add_argument("--cg-iterations", type=int, default=312,
+                    help="FP64 CG iterations of this workload (reference arm extrapolation)")
+    ap.add_argument("--dslash-only", default=None, help="profiling target: only time M in this precision")
+    ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.dslash_only:
+        return run_dslash_only(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

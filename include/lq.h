@@ -1,0 +1,162 @@
+/*
+ * lq.h - C interface of a GB300 (sm_103a) library for two-flavour
+ * Wilson-fermion Hybrid Monte Carlo, following Chakrabarty & Majumdar,
+ * "Hybrid Monte Carlo with Wilson Dirac operator on the Fermi GPU".
+ *
+ * The paper's program applies the Wilson-Dirac matrix M = D + m and its
+ * adjoint to the pseudofermion field inside a conjugate-gradient inversion
+ * of M^dag M (Eq. 4, Sec. 1 and Sec. 3 kernel 1), computes the gauge and
+ * fermion driving forces (Sec. 3 kernels 2 and 3), evolves momenta and
+ * links by leapfrog (Sec. 3 kernel 4; Sec. 2) and accepts or rejects the
+ * trajectory on H_new - H_old (Eq. 5; Sec. 3, trajectory step 3).  Each
+ * entry point below is one of those operations.
+ *
+ * Conventions (the paper fixes none of them; these are the readings the
+ * library takes and its tests pin):
+ *   lattice     Lx x Ly x Lz x Lt, direction mu = 0..3 = x, y, z, t,
+ *               site s = x + Lx*(y + Ly*(z + Lz*t))
+ *   operator    M psi(x) = psi(x) - kappa sum_mu [ (1 - g_mu) U_mu(x) psi(x+mu)
+ *                                              + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu) ]
+ *               (Wilson r = 1, hopping-parameter normalisation, M^dag = g5 M g5),
+ *               gamma matrices in the DeGrand-Rossi basis
+ *   boundary    periodic in x, y, z; antiperiodic in t when t_antiperiodic != 0
+ *   su(3)       t_a = lambda_a / sqrt(2), p = sum_a p_a t_a, kinetic term (1/2) sum p_a^2
+ *
+ * Canonical buffer layouts (all FP64, complex numbers interleaved re, im):
+ *   gauge field   double [V][4][3][3][2]   U_mu(s) row-major
+ *   spinor        double [V][4][3][2]      spin-major, colour fastest
+ *   momentum /
+ *   force         double [V][4][8]         su(3) coefficients
+ * Every buffer argument may live in device memory or in host memory (the
+ * library asks the CUDA runtime which).  Buffers must be 16-byte aligned.
+ * The caller owns every buffer it passes; the context owns its internal
+ * copies (site-major structure-of-arrays, several precisions) and
+ * workspaces, and frees them in lq_destroy.
+ *
+ * Ordering: work is issued on the context's CUDA stream.  A call whose
+ * arguments are all device buffers and that returns no host scalar is
+ * asynchronous; a call that writes a host buffer or a host scalar
+ * synchronises the stream before it returns.
+ *
+ * Errors: every call returns an lq_status; nothing throws across this
+ * interface.  lq_last_error() returns a description of the last failure
+ * on that context.  A context must not be used from two host threads at
+ * the same time.
+ */
+#ifndef LQ_H
+#define LQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lq_ctx lq_ctx;
+
+typedef enum {
+  LQ_OK = 0,
+  LQ_ERR_ARG = 1,            /* bad argument: null pointer, misaligned buffer, bad precision, ... */
+  LQ_ERR_SHAPE = 2,          /* lattice extents not allowed */
+  LQ_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  LQ_ERR_NOT_CONVERGED = 4,  /* iteration limit reached; the best iterate was still written */
+  LQ_ERR_NAN = 5,            /* a non-finite value appeared (input or breakdown) */
+  LQ_ERR_STATE = 6           /* call out of order, e.g. no gauge field set yet */
+} lq_status;
+
+/* Storage / arithmetic precision of the operator and of the inner solver.
+ *   LQ_F64      FP64 links (18 reals) and spinors, FP64 arithmetic
+ *   LQ_F32      FP32 links (18 reals) and spinors, FP32 arithmetic
+ *   LQ_F32_12   FP32 links stored as 12 reals (row 3 rebuilt), FP32 spinors
+ *   LQ_F16_12   FP16 links (12 reals), FP16 spinors scaled by a per-site FP32 norm,
+ *               FP32 arithmetic
+ *   LQ_BF16_12  as LQ_F16_12 with BF16 storage */
+typedef enum { LQ_F64 = 0, LQ_F32 = 1, LQ_F32_12 = 2, LQ_F16_12 = 3, LQ_BF16_12 = 4 } lq_prec;
+
+typedef struct {
+  int iterations;           /* CG iterations (inner iterations for a mixed solve) */
+  int reliable_updates;     /* FP64 true-residual recomputations that fed back into the solve */
+  int restarts;             /* restarts of the search direction from the true residual */
+  int converged;            /* 1 when true_rel_resid <= tol */
+  double true_rel_resid;    /* ||phi - M^dag M x|| / ||phi||, recomputed in FP64 */
+  double seconds;           /* host wall-clock of the call, from entry to the final synchronisation */
+  int64_t kernel_launches;  /* kernels this call launched (every node of a CUDA graph counts once) */
+} lq_solve_stats;
+
+/* Library version string. */
+const char* lq_version(void);
+
+/* Create a context for an Lx x Ly x Lz x Lt lattice (dims[0..3] = Lx, Ly,
+ * Lz, Lt, each >= 2, V = product < 2^31 / 64), on the current CUDA device,
+ * issuing work on `cuda_stream` (a cudaStream_t; NULL = the legacy default
+ * stream).  Lattice of Sec. 1 ("Lambda", N_site points, d x N_site links).
+ * Errors: LQ_ERR_ARG (null out), LQ_ERR_SHAPE, LQ_ERR_CUDA. */
+lq_status lq_create(lq_ctx** out, const int dims[4], int t_antiperiodic, void* cuda_stream);
+
+/* Free the context and everything it owns.  Synchronises its stream. */
+lq_status lq_destroy(lq_ctx* ctx);
+
+/* Description of the last error on ctx (never NULL; "" when none). */
+const char* lq_last_error(const lq_ctx* ctx);
+
+/* Issue subsequent work on another stream (a cudaStream_t). */
+lq_status lq_set_stream(lq_ctx* ctx, void* cuda_stream);
+
+/* Number of lattice sites V. */
+int64_t lq_volume(const lq_ctx* ctx);
+
+/* Load the gauge field U_{n,mu} in SU(3) (Sec. 1: "U_{n,mu} ... defined on
+ * the link (n, mu)"), canonical layout, host or device.  Low-precision
+ * copies are rebuilt from it on first use.  Links stored with 12 reals are
+ * reconstructed assuming det U = 1.  Errors: LQ_ERR_ARG. */
+lq_status lq_gauge_set(lq_ctx* ctx, const double* U);
+
+/* Copy the context's current gauge field to U (canonical layout). */
+lq_status lq_gauge_get(lq_ctx* ctx, double* U);
+
+/* out = M in (dagger = 0) or M^dag in (dagger = 1) in precision `prec`
+ * (Eq. 4; Sec. 3 kernel 1: the Dirac operator and its hermitian conjugate
+ * acting on the pseudofermion field).  in and out are canonical spinors
+ * and must not overlap.  Low precisions convert on the way in and out.
+ * Errors: LQ_ERR_ARG, LQ_ERR_STATE (no gauge field). */
+lq_status lq_apply_M(lq_ctx* ctx, double* out, const double* in, double kappa, int dagger, int prec);
+
+/* out = M^dag M in, precision `prec` (the matrix of Eq. 4). */
+lq_status lq_apply_MdagM(lq_ctx* ctx, double* out, const double* in, double kappa, int prec);
+
+/* Solve M^dag M x = phi by conjugate gradient (Sec. 1 after Eq. 3; Sec. 3,
+ * "conjugate gradient routine") from x0 = 0, until the FP64 true residual
+ * ||phi - M^dag M x|| / ||phi|| <= tol.
+ *   inner_prec      LQ_F64: plain FP64 CG.  Otherwise the iterations run
+ *                   in that precision and the solution and residual are
+ *                   corrected in FP64 ("reliable updates"): at least every
+ *                   `reliable_every` iterations (0 = only when the iterated
+ *                   residual has dropped by 1e-2 since the last update, or
+ *                   has met tol) the low-precision solution is added to
+ *                   the FP64 one and the FP64 residual is recomputed.
+ *   maxiter         iteration limit (> 0)
+ *   hist, hist_len  optional host array receiving the relative iterated
+ *                   residual of each iteration (NULL / 0 to skip)
+ *   stats           optional, filled on return
+ * x receives the FP64 solution, also when LQ_ERR_NOT_CONVERGED is returned.
+ * phi = 0 gives x = 0.  Synchronises.  Errors: LQ_ERR_ARG, LQ_ERR_STATE,
+ * LQ_ERR_NOT_CONVERGED, LQ_ERR_NAN (non-finite input or CG breakdown). */
+lq_status lq_solve_MdagM(lq_ctx* ctx, double* x, const double* phi, double kappa, double tol, int maxiter,
+                         int inner_prec, int reliable_every, double* hist, int hist_len,
+                         lq_solve_stats* stats);
+
+/* Measurement: apply M (dagger = 0) or M^dag (1) `n` times in precision
+ * `prec` to `in` (packed once, outside the timed region) and return the
+ * average device time of one application in *ms, measured with CUDA events
+ * on the context's stream.  flush_l2 != 0 writes a 256 MB buffer before
+ * each application (outside its timing) so no operand is L2-resident.
+ * This is the hot kernel of the solve (Sec. 2: repeated multiplication of
+ * M takes most of the molecular-dynamics time).  Synchronises. */
+lq_status lq_time_dslash(lq_ctx* ctx, const double* in, double kappa, int dagger, int prec, int n, int flush_l2,
+                         double* ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQ_H */

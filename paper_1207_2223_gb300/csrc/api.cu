@@ -1,0 +1,494 @@
+// C interface (include/lq.h): context management, buffer staging between
+// the canonical layout and the internal formats, and the host driver of
+// the CG solver (paper Sec. 3: the host sets up fields and calls the
+// kernels; all vectors stay resident on the GPU, only scalars come back).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "lq_internal.h"
+
+using namespace lq;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+lq_status fail(lq_ctx* c, lq_status code, const std::string& msg) {
+  if (c) c->last_error = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+lq_status cuda_check(lq_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return LQ_OK;
+  cudaGetLastError();
+  return fail(c, LQ_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LQ_TRY(expr)                         \
+  do {                                       \
+    lq_status _s = (expr);                   \
+    if (_s != LQ_OK) return _s;              \
+  } while (0)
+#define LQ_CUDA(c, call) LQ_TRY(cuda_check((c), (call), #call))
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+lq_status alloc_field(lq_ctx* c, Field& f, SStore s) {
+  if (f.data) return LQ_OK;
+  f.store = s;
+  LQ_CUDA(c, cudaMalloc(&f.data, spinor_bytes(s, c->geo.V)));
+  if (s == SStore::F16 || s == SStore::BF16) LQ_CUDA(c, cudaMalloc(&f.norm, sizeof(float) * c->geo.V));
+  return LQ_OK;
+}
+
+void free_field(Field& f) {
+  if (f.data) cudaFree(f.data);
+  if (f.norm) cudaFree(f.norm);
+  f.data = nullptr;
+  f.norm = nullptr;
+}
+
+lq_status require_gauge(lq_ctx* c, int prec) {
+  if (!c->gauge_set) return fail(c, LQ_ERR_STATE, "no gauge field set (call lq_gauge_set first)");
+  if (prec == LQ_F64) return LQ_OK;
+  if (!c->gauge_lo[prec]) LQ_CUDA(c, cudaMalloc(&c->gauge_lo[prec], gauge_bytes(gauge_store_of(prec), c->geo.V)));
+  if (!c->gauge_lo_valid[prec]) {
+    launch_convert_gauge(c->geo, c->gauge64, gauge_store_of(prec), c->gauge_lo[prec], c->stream);
+    LQ_CUDA(c, cudaGetLastError());
+    c->gauge_lo_valid[prec] = true;
+  }
+  return LQ_OK;
+}
+
+lq_status check_prec(lq_ctx* c, int prec) {
+  if (prec < LQ_F64 || prec > LQ_BF16_12) return fail(c, LQ_ERR_ARG, "unknown precision");
+  return LQ_OK;
+}
+
+// Canonical spinor (host or device) -> device pointer to canonical data.
+lq_status stage_spinor_in(lq_ctx* c, const double* in, const double** dev) {
+  if (!in) return fail(c, LQ_ERR_ARG, "null spinor buffer");
+  if (!aligned16(in)) return fail(c, LQ_ERR_ARG, "spinor buffer not 16-byte aligned");
+  if (is_device_ptr(in)) { *dev = in; return LQ_OK; }
+  LQ_CUDA(c, cudaMemcpyAsync(c->stage_in, in, sizeof(double) * 24 * c->geo.V, cudaMemcpyHostToDevice, c->stream));
+  *dev = c->stage_in;
+  return LQ_OK;
+}
+
+// Unpack a field to the caller's canonical buffer (host or device).
+lq_status deliver_spinor(lq_ctx* c, const Field& f, double* out) {
+  if (!out) return fail(c, LQ_ERR_ARG, "null output buffer");
+  if (!aligned16(out)) return fail(c, LQ_ERR_ARG, "output buffer not 16-byte aligned");
+  if (is_device_ptr(out)) {
+    launch_unpack_spinor(c->geo, f.store, f.ref(), out, c->stream);
+    LQ_CUDA(c, cudaGetLastError());
+    return LQ_OK;
+  }
+  launch_unpack_spinor(c->geo, f.store, f.ref(), c->stage_out, c->stream);
+  LQ_CUDA(c, cudaGetLastError());
+  LQ_CUDA(c, cudaMemcpyAsync(out, c->stage_out, sizeof(double) * 24 * c->geo.V, cudaMemcpyDeviceToHost, c->stream));
+  LQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LQ_OK;
+}
+
+lq_status ensure_solver_fields(lq_ctx* c, int inner) {
+  LQ_TRY(alloc_field(c, c->phi64, SStore::F64));
+  LQ_TRY(alloc_field(c, c->x64, SStore::F64));
+  LQ_TRY(alloc_field(c, c->r64, SStore::F64));
+  LQ_TRY(alloc_field(c, c->tmp64, SStore::F64));
+  if (inner == LQ_F64) {
+    LQ_TRY(alloc_field(c, c->p64, SStore::F64));
+    LQ_TRY(alloc_field(c, c->t64, SStore::F64));
+  } else {
+    const SStore s = spinor_store_of(inner);
+    const int k = (int)s;
+    LQ_TRY(alloc_field(c, c->r_lo[k], s));
+    LQ_TRY(alloc_field(c, c->p_lo[k], s));
+    LQ_TRY(alloc_field(c, c->t_lo[k], s));
+    LQ_TRY(alloc_field(c, c->x_lo[k], s));
+  }
+  return LQ_OK;
+}
+
+// Run n CG iterations as one CUDA graph (recorded once per context,
+// precision, length and kappa); the kernels return at once after the
+// device-side halt flag is raised.
+lq_status run_chunk(lq_ctx* c, int inner, int n, double kappa) {
+  auto key = std::make_tuple(0, inner, n, kappa);
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    LQ_CUDA(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < n; ++i) {
+      if (inner == LQ_F64) cg64_iteration(c, kappa, c->capture_stream);
+      else cglo_iteration(c, inner, kappa, c->capture_stream);
+    }
+    LQ_CUDA(c, cudaStreamEndCapture(c->capture_stream, &graph));
+    GraphEntry e;
+    cudaError_t err = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    LQ_CUDA(c, err);
+    it = c->graphs.emplace(key, e).first;
+  }
+  LQ_CUDA(c, cudaGraphLaunch(it->second.exec, c->stream));
+  return LQ_OK;
+}
+
+lq_status read_state(lq_ctx* c) {
+  LQ_CUDA(c, cudaMemcpyAsync(c->state_host, c->state, sizeof(SolverState), cudaMemcpyDeviceToHost, c->stream));
+  LQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lq_version(void) { return "lq 0.1 (sm_103a)"; }
+
+lq_status lq_create(lq_ctx** out, const int dims[4], int t_antiperiodic, void* cuda_stream) {
+  if (!out || !dims) return fail(nullptr, LQ_ERR_ARG, "null argument");
+  *out = nullptr;
+  long long V = 1;
+  for (int m = 0; m < 4; ++m) {
+    if (dims[m] < 2) return fail(nullptr, LQ_ERR_SHAPE, "every lattice extent must be >= 2");
+    V *= dims[m];
+  }
+  if (V >= (1LL << 31) / 64) return fail(nullptr, LQ_ERR_SHAPE, "lattice volume too large");
+  lq_ctx* c = new lq_ctx();
+  c->geo.V = (int)V;
+  for (int m = 0; m < 4; ++m) c->geo.L[m] = dims[m];
+  c->geo.stride[0] = 1;
+  for (int m = 1; m < 4; ++m) c->geo.stride[m] = c->geo.stride[m - 1] * dims[m - 1];
+  c->geo.antiperiodic = t_antiperiodic ? 1 : 0;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  lq_status st = LQ_OK;
+  auto chk = [&](cudaError_t e, const char* what) {
+    if (st == LQ_OK && e != cudaSuccess) {
+      cudaGetLastError();
+      g_create_error = std::string(what) + ": " + cudaGetErrorString(e);
+      st = LQ_ERR_CUDA;
+    }
+  };
+  chk(cudaGetDevice(&c->device), "cudaGetDevice");
+  chk(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  const size_t spin = sizeof(double) * 24 * (size_t)V;
+  chk(cudaMalloc(&c->gauge64, gauge_bytes(GStore::F64_18, (int)V)), "cudaMalloc gauge");
+  chk(cudaMalloc(&c->stage_in, spin), "cudaMalloc stage");
+  chk(cudaMalloc(&c->stage_out, spin), "cudaMalloc stage");
+  c->rs.max_blocks = (int)((V + 63) / 64) + 1;
+  chk(cudaMalloc(&c->rs.partials, sizeof(double) * 4 * c->rs.max_blocks), "cudaMalloc partials");
+  chk(cudaMalloc(&c->rs.ticket, sizeof(unsigned int) * 4), "cudaMalloc ticket");
+  if (st == LQ_OK) chk(cudaMemset(c->rs.ticket, 0, sizeof(unsigned int) * 4), "cudaMemset");
+  chk(cudaMalloc(&c->state, sizeof(SolverState)), "cudaMalloc state");
+  chk(cudaMallocHost(&c->state_host, sizeof(SolverState)), "cudaMallocHost");
+  chk(cudaMalloc(&c->dscalar, sizeof(double) * 8), "cudaMalloc scalars");
+  chk(cudaMallocHost(&c->dscalar_host, sizeof(double) * 8), "cudaMallocHost");
+  if (st != LQ_OK) {
+    lq_destroy(c);
+    return st;
+  }
+  *out = c;
+  return LQ_OK;
+}
+
+lq_status lq_destroy(lq_ctx* c) {
+  if (!c) return LQ_OK;
+  cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  if (c->gauge64) cudaFree(c->gauge64);
+  for (int p = 0; p < kNumPrec; ++p)
+    if (c->gauge_lo[p]) cudaFree(c->gauge_lo[p]);
+  if (c->stage_in) cudaFree(c->stage_in);
+  if (c->stage_out) cudaFree(c->stage_out);
+  if (c->stage_gauge) cudaFree(c->stage_gauge);
+  for (Field* f : {&c->phi64, &c->x64, &c->r64, &c->p64, &c->t64, &c->tmp64}) free_field(*f);
+  for (int k = 0; k < 4; ++k) {
+    free_field(c->r_lo[k]);
+    free_field(c->p_lo[k]);
+    free_field(c->t_lo[k]);
+    free_field(c->x_lo[k]);
+  }
+  if (c->rs.partials) cudaFree(c->rs.partials);
+  if (c->rs.ticket) cudaFree(c->rs.ticket);
+  if (c->state) cudaFree(c->state);
+  if (c->state_host) cudaFreeHost(c->state_host);
+  if (c->dscalar) cudaFree(c->dscalar);
+  if (c->dscalar_host) cudaFreeHost(c->dscalar_host);
+  delete c;
+  return LQ_OK;
+}
+
+const char* lq_last_error(const lq_ctx* c) { return c ? c->last_error.c_str() : g_create_error.c_str(); }
+
+lq_status lq_set_stream(lq_ctx* c, void* cuda_stream) {
+  if (!c) return LQ_ERR_ARG;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  return LQ_OK;
+}
+
+int64_t lq_volume(const lq_ctx* c) { return c ? (int64_t)c->geo.V : 0; }
+
+lq_status lq_gauge_set(lq_ctx* c, const double* U) {
+  if (!c) return LQ_ERR_ARG;
+  if (!U) return fail(c, LQ_ERR_ARG, "null gauge buffer");
+  if (!aligned16(U)) return fail(c, LQ_ERR_ARG, "gauge buffer not 16-byte aligned");
+  const double* src = U;
+  if (!is_device_ptr(U)) {
+    if (!c->stage_gauge) LQ_CUDA(c, cudaMalloc(&c->stage_gauge, sizeof(double) * 72 * (size_t)c->geo.V));
+    LQ_CUDA(c, cudaMemcpyAsync(c->stage_gauge, U, sizeof(double) * 72 * (size_t)c->geo.V, cudaMemcpyHostToDevice,
+                               c->stream));
+    src = c->stage_gauge;
+  }
+  launch_pack_gauge64(c->geo, src, c->gauge64, c->stream);
+  LQ_CUDA(c, cudaGetLastError());
+  for (int p = 0; p < kNumPrec; ++p) c->gauge_lo_valid[p] = false;
+  c->gauge_set = true;
+  if (src != U) LQ_CUDA(c, cudaStreamSynchronize(c->stream));   // the host buffer may be reused at once
+  return LQ_OK;
+}
+
+lq_status lq_gauge_get(lq_ctx* c, double* U) {
+  if (!c) return LQ_ERR_ARG;
+  if (!c->gauge_set) return fail(c, LQ_ERR_STATE, "no gauge field set");
+  if (!U) return fail(c, LQ_ERR_ARG, "null gauge buffer");
+  if (!aligned16(U)) return fail(c, LQ_ERR_ARG, "gauge buffer not 16-byte aligned");
+  if (is_device_ptr(U)) {
+    launch_unpack_gauge64(c->geo, c->gauge64, U, c->stream);
+    LQ_CUDA(c, cudaGetLastError());
+    return LQ_OK;
+  }
+  if (!c->stage_gauge) LQ_CUDA(c, cudaMalloc(&c->stage_gauge, sizeof(double) * 72 * (size_t)c->geo.V));
+  launch_unpack_gauge64(c->geo, c->gauge64, c->stage_gauge, c->stream);
+  LQ_CUDA(c, cudaGetLastError());
+  LQ_CUDA(c, cudaMemcpyAsync(U, c->stage_gauge, sizeof(double) * 72 * (size_t)c->geo.V, cudaMemcpyDeviceToHost,
+                             c->stream));
+  LQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LQ_OK;
+}
+
+lq_status lq_apply_M(lq_ctx* c, double* out, const double* in, double kappa, int dagger, int prec) {
+  if (!c) return LQ_ERR_ARG;
+  LQ_TRY(check_prec(c, prec));
+  LQ_TRY(require_gauge(c, prec));
+  if (in == out) return fail(c, LQ_ERR_ARG, "in and out must not overlap");
+  const SStore s = spinor_store_of(prec);
+  Field& fin = (prec == LQ_F64) ? c->phi64 : c->p_lo[(int)s];
+  Field& fout = (prec == LQ_F64) ? c->tmp64 : c->t_lo[(int)s];
+  LQ_TRY(alloc_field(c, fin, s));
+  LQ_TRY(alloc_field(c, fout, s));
+  const double* din = nullptr;
+  LQ_TRY(stage_spinor_in(c, in, &din));
+  launch_pack_spinor(c->geo, din, s, fin.ref(), c->stream);
+  const void* gauge = prec == LQ_F64 ? c->gauge64 : c->gauge_lo[prec];
+  apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream);
+  LQ_CUDA(c, cudaGetLastError());
+  return deliver_spinor(c, fout, out);
+}
+
+lq_status lq_apply_MdagM(lq_ctx* c, double* out, const double* in, double kappa, int prec) {
+  if (!c) return LQ_ERR_ARG;
+  LQ_TRY(check_prec(c, prec));
+  LQ_TRY(require_gauge(c, prec));
+  if (in == out) return fail(c, LQ_ERR_ARG, "in and out must not overlap");
+  const SStore s = spinor_store_of(prec);
+  Field& fin = (prec == LQ_F64) ? c->phi64 : c->p_lo[(int)s];
+  Field& fmid = (prec == LQ_F64) ? c->tmp64 : c->t_lo[(int)s];
+  Field& fout = (prec == LQ_F64) ? c->r64 : c->r_lo[(int)s];
+  LQ_TRY(alloc_field(c, fin, s));
+  LQ_TRY(alloc_field(c, fmid, s));
+  LQ_TRY(alloc_field(c, fout, s));
+  const double* din = nullptr;
+  LQ_TRY(stage_spinor_in(c, in, &din));
+  launch_pack_spinor(c->geo, din, s, fin.ref(), c->stream);
+  const void* gauge = prec == LQ_F64 ? c->gauge64 : c->gauge_lo[prec];
+  apply_M_prec(c->geo, prec, gauge, fin.ref(), fmid.ref(), kappa, false, c->stream);
+  apply_M_prec(c->geo, prec, gauge, fmid.ref(), fout.ref(), kappa, true, c->stream);
+  LQ_CUDA(c, cudaGetLastError());
+  return deliver_spinor(c, fout, out);
+}
+
+lq_status lq_solve_MdagM(lq_ctx* c, double* x, const double* phi, double kappa, double tol, int maxiter,
+                         int inner, int reliable_every, double* hist, int hist_len, lq_solve_stats* stats) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!c) return LQ_ERR_ARG;
+  LQ_TRY(check_prec(c, inner));
+  if (!(tol > 0.0) || maxiter <= 0 || reliable_every < 0 || (hist && hist_len < 0))
+    return fail(c, LQ_ERR_ARG, "bad tolerance, iteration limit or history length");
+  LQ_TRY(require_gauge(c, LQ_F64));
+  LQ_TRY(require_gauge(c, inner));
+  LQ_TRY(ensure_solver_fields(c, inner));
+  const Geom& g = c->geo;
+  const bool mixed = inner != LQ_F64;
+  const SStore slo = spinor_store_of(inner);
+  const int k = (int)slo;
+
+  double* hist_dev = nullptr;
+  if (hist && hist_len > 0) LQ_CUDA(c, cudaMallocAsync((void**)&hist_dev, sizeof(double) * hist_len, c->stream));
+
+  const double* dphi = nullptr;
+  LQ_TRY(stage_spinor_in(c, phi, &dphi));
+  launch_pack_spinor(g, dphi, SStore::F64, c->phi64.ref(), c->stream);
+
+  SolverState h{};
+  h.stop2 = tol * tol;
+  h.ru_every = mixed ? reliable_every : 0;
+  h.delta2 = mixed ? 1e-4 : 0.0;          // reliable update once |r| fell by 1e-2
+  h.maxiter = maxiter;
+  h.hist = hist_dev;
+  h.hist_len = hist_dev ? hist_len : 0;
+  *c->state_host = h;
+  LQ_CUDA(c, cudaMemcpyAsync(c->state, c->state_host, sizeof(SolverState), cudaMemcpyHostToDevice, c->stream));
+  if (mixed) {
+    launch_zero_spinor(g, SStore::F64, c->x64.ref(), c->stream);
+    launch_solver_init(g, c->phi64.ref(), slo, c->x_lo[k].ref(), slo, c->r_lo[k].ref(), slo, c->p_lo[k].ref(),
+                       c->state, c->rs, c->stream);
+  } else {
+    launch_solver_init(g, c->phi64.ref(), SStore::F64, c->x64.ref(), SStore::F64, c->r64.ref(), SStore::F64,
+                       c->p64.ref(), c->state, c->rs, c->stream);
+  }
+  LQ_CUDA(c, cudaGetLastError());
+  LQ_TRY(read_state(c));
+
+  lq_solve_stats s{};
+  s.kernel_launches = mixed ? 3 : 2;      // pack phi, (zero x,) initialise
+  lq_status result = LQ_OK;
+  double rel = 1.0;
+  if (c->state_host->breakdown) {
+    result = fail(c, LQ_ERR_NAN, "non-finite right-hand side");
+  } else if (c->state_host->phi2 == 0.0) {
+    rel = 0.0;
+    s.converged = 1;
+  } else {
+    const int chunk = mixed ? (reliable_every > 0 ? reliable_every : 32) : 16;
+    double best_rr = c->state_host->phi2;
+    int stagnant = 0;
+    for (long guard = 0; guard < (long)maxiter + 64; ++guard) {
+      LQ_TRY(run_chunk(c, inner, chunk, kappa));
+      s.kernel_launches += 3 * chunk;
+      LQ_TRY(read_state(c));
+      const SolverState& st = *c->state_host;
+      if (st.breakdown) { result = fail(c, LQ_ERR_NAN, "CG breakdown (non-positive or non-finite curvature)"); break; }
+      if (!st.halt) continue;
+      // true residual in FP64; for mixed solves this is the reliable update
+      if (mixed) launch_accumulate_x(g, slo, c->x_lo[k].ref(), c->x64.ref(), c->stream);
+      cg64_true_residual(c, kappa, inner, c->stream);
+      s.kernel_launches += mixed ? 3 : 2;
+      LQ_CUDA(c, cudaGetLastError());
+      LQ_TRY(read_state(c));
+      const double rr_true = c->state_host->rr_true;
+      rel = std::sqrt(rr_true / c->state_host->phi2);
+      if (mixed) s.reliable_updates++;
+      if (!std::isfinite(rel)) { result = fail(c, LQ_ERR_NAN, "non-finite residual"); break; }
+      if (rel <= tol) { s.converged = 1; break; }
+      if (c->state_host->iter >= maxiter) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "not converged after %d iterations (relative residual %.3e)",
+                      c->state_host->iter, rel);
+        result = fail(c, LQ_ERR_NOT_CONVERGED, buf);
+        break;
+      }
+      // FP64 CG: the recursion met tol but the true residual did not ->
+      // restart from the true residual.  Mixed: keep the search direction
+      // unless the true residual has stopped improving.
+      int restart = mixed ? 0 : 1;
+      if (mixed) {
+        if (rr_true < 0.5 * best_rr) { best_rr = rr_true; stagnant = 0; }
+        else if (++stagnant >= 3) { restart = 1; stagnant = 0; }
+      }
+      if (restart) s.restarts++;
+      launch_state_after_residual(c->state, restart, c->stream);
+      if (mixed) launch_xpay_p(g, slo, c->r_lo[k].ref(), c->p_lo[k].ref(), c->state, true, c->stream);
+      else launch_xpay_p(g, SStore::F64, c->r64.ref(), c->p64.ref(), c->state, true, c->stream);
+      s.kernel_launches += 2;
+      LQ_CUDA(c, cudaGetLastError());
+    }
+  }
+  s.iterations = c->state_host->iter;
+  s.true_rel_resid = rel;
+  if (result == LQ_OK || result == LQ_ERR_NOT_CONVERGED) {
+    lq_status d = deliver_spinor(c, c->x64, x);
+    s.kernel_launches += 1;
+    if (d != LQ_OK) result = d;
+  }
+  if (hist_dev) {
+    const int n = s.iterations < hist_len ? s.iterations : hist_len;
+    if (n > 0) cudaMemcpyAsync(hist, hist_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(hist_dev, c->stream);
+  }
+  lq_status fin = cuda_check(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (result == LQ_OK) result = fin;
+  s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = s;
+  return result;
+}
+
+lq_status lq_time_dslash(lq_ctx* c, const double* in, double kappa, int dagger, int prec, int n, int flush_l2,
+                         double* ms) {
+  if (!c) return LQ_ERR_ARG;
+  if (!ms || n <= 0) return fail(c, LQ_ERR_ARG, "need n > 0 and an output pointer");
+  LQ_TRY(check_prec(c, prec));
+  LQ_TRY(require_gauge(c, prec));
+  const SStore s = spinor_store_of(prec);
+  Field& fin = (prec == LQ_F64) ? c->phi64 : c->p_lo[(int)s];
+  Field& fout = (prec == LQ_F64) ? c->tmp64 : c->t_lo[(int)s];
+  LQ_TRY(alloc_field(c, fin, s));
+  LQ_TRY(alloc_field(c, fout, s));
+  const double* din = nullptr;
+  LQ_TRY(stage_spinor_in(c, in, &din));
+  launch_pack_spinor(c->geo, din, s, fin.ref(), c->stream);
+  const void* gauge = prec == LQ_F64 ? c->gauge64 : c->gauge_lo[prec];
+  const size_t flush_bytes = (size_t)256 << 20;
+  void* flush = nullptr;
+  if (flush_l2) LQ_CUDA(c, cudaMallocAsync(&flush, flush_bytes, c->stream));
+  cudaEvent_t e0, e1;
+  LQ_CUDA(c, cudaEventCreate(&e0));
+  LQ_CUDA(c, cudaEventCreate(&e1));
+  apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream);   // warm-up
+  double total = 0.0;
+  lq_status st = LQ_OK;
+  if (flush_l2) {
+    for (int i = 0; i < n && st == LQ_OK; ++i) {
+      cudaMemsetAsync(flush, i & 0xff, flush_bytes, c->stream);
+      cudaEventRecord(e0, c->stream);
+      apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream);
+      cudaEventRecord(e1, c->stream);
+      st = cuda_check(c, cudaEventSynchronize(e1), "cudaEventSynchronize");
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      total += t;
+    }
+  } else {
+    cudaEventRecord(e0, c->stream);
+    for (int i = 0; i < n; ++i)
+      apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream);
+    cudaEventRecord(e1, c->stream);
+    st = cuda_check(c, cudaEventSynchronize(e1), "cudaEventSynchronize");
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    total = t;
+  }
+  if (st == LQ_OK) st = cuda_check(c, cudaGetLastError(), "dslash launch");
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (flush) cudaFreeAsync(flush, c->stream);
+  cudaStreamSynchronize(c->stream);
+  *ms = total / n;
+  return st;
+}
+
+}  // extern "C"

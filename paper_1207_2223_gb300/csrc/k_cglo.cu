@@ -1,0 +1,32 @@
+// Low-precision CG iteration for mixed-precision solves: the same three
+// fused passes as the FP64 iteration, on FP32 or 16-bit storage with FP32
+// arithmetic and FP64 reductions.  The FP64 solution and residual are
+// corrected by reliable updates driven from the host (api.cu).
+#include "lq_internal.h"
+
+namespace lq {
+
+template <GStore G, SStore S>
+static void iteration(lq_ctx* c, const void* gauge, double kappa, cudaStream_t stream) {
+  const Geom& g = c->geo;
+  GaugeRef U{gauge};
+  const int k = (int)S;
+  EpiCG1<S> e1{c->t_lo[k].ref(), c->state};
+  launch_dslash<float, G, S, false>(g, U, c->p_lo[k].ref(), kappa, e1, c->rs, stream);
+  EpiCG2<S, S, S> e2{c->r_lo[k].ref(), c->x_lo[k].ref(), c->p_lo[k].ref(), c->state};
+  launch_dslash<float, G, S, true>(g, U, c->t_lo[k].ref(), kappa, e2, c->rs, stream);
+  launch_xpay_p(g, S, c->r_lo[k].ref(), c->p_lo[k].ref(), c->state, false, stream);
+}
+
+void cglo_iteration(lq_ctx* c, int prec, double kappa, cudaStream_t stream) {
+  const void* gauge = c->gauge_lo[prec];
+  switch (prec) {
+    case LQ_F32: iteration<GStore::F32_18, SStore::F32>(c, gauge, kappa, stream); break;
+    case LQ_F32_12: iteration<GStore::F32_12, SStore::F32>(c, gauge, kappa, stream); break;
+    case LQ_F16_12: iteration<GStore::F16_12, SStore::F16>(c, gauge, kappa, stream); break;
+    case LQ_BF16_12: iteration<GStore::BF16_12, SStore::BF16>(c, gauge, kappa, stream); break;
+    default: break;
+  }
+}
+
+}  // namespace lq

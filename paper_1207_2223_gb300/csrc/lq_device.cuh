@@ -1,0 +1,372 @@
+// Device-side building blocks of the lattice library: complex arithmetic,
+// the site-major structure-of-arrays storage formats of gauge links and
+// spinors, the Wilson spin projectors, and a deterministic grid reduction.
+//
+// Storage formats (every array is [chunk][site]: consecutive threads read
+// consecutive 8- or 16-byte words, so every load and store is coalesced):
+//   spinor F64   double2 [12][V]          complex c = 3*spin + colour
+//   spinor F32   float4  [6][V]           chunk k holds complex 2k, 2k+1
+//   spinor F16 / BF16  uint4 [3][V] + float norm[V]
+//                chunk k holds reals 8k..8k+7 (re, im interleaved) scaled by
+//                1/norm, norm = max |real| of the site (0 for a zero site)
+//   gauge F64_18 double2 [4][9][V]        U_mu(x) row-major, complex (i,j) = 3i+j
+//   gauge F32_18 float2  [4][9][V]
+//   gauge F32_12 float4  [4][3][V]        rows 0, 1 only (12 reals)
+//   gauge F16_12 / BF16_12  uint2 [4][3][V]  rows 0, 1 only, 4 reals per chunk
+// Links stored with 12 reals are rebuilt on the fly with
+// row 2 = conj(row 0 x row 1), exact for SU(3).  The antiperiodic time
+// boundary is applied as a sign on the hop, never folded into links, so
+// the reconstruction stays valid.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <type_traits>
+
+namespace lq {
+
+template <typename T> struct cplx { T re, im; };
+
+template <typename T> __device__ __forceinline__ cplx<T> mk(T a, T b) { return {a, b}; }
+template <typename T> __device__ __forceinline__ cplx<T> operator+(cplx<T> a, cplx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T> __device__ __forceinline__ cplx<T> operator-(cplx<T> a, cplx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T> __device__ __forceinline__ cplx<T> operator-(cplx<T> a) { return {-a.re, -a.im}; }
+template <typename T> __device__ __forceinline__ cplx<T> operator*(T s, cplx<T> a) { return {s * a.re, s * a.im}; }
+template <typename T> __device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// conj(a) * b
+template <typename T> __device__ __forceinline__ cplx<T> cjmul(cplx<T> a, cplx<T> b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+// acc + a * b
+template <typename T> __device__ __forceinline__ cplx<T> cmadd(cplx<T> acc, cplx<T> a, cplx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re); acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im); acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
+// acc + conj(a) * b
+template <typename T> __device__ __forceinline__ cplx<T> cjmadd(cplx<T> acc, cplx<T> a, cplx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re); acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im); acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+template <typename T> __device__ __forceinline__ cplx<T> times_i(cplx<T> a) { return {-a.im, a.re}; }
+template <typename T> __device__ __forceinline__ cplx<T> conjg(cplx<T> a) { return {a.re, -a.im}; }
+template <typename T> __device__ __forceinline__ T norm2(cplx<T> a) { return a.re * a.re + a.im * a.im; }
+
+// ---------------------------------------------------------------- formats
+enum class SStore : int { F64 = 0, F32 = 1, F16 = 2, BF16 = 3 };
+enum class GStore : int { F64_18 = 0, F32_18 = 1, F32_12 = 2, F16_12 = 3, BF16_12 = 4 };
+
+struct SpinorRef {           // device view of one spinor field
+  void* p;                   // chunk array
+  float* norm;               // per-site norm (F16 / BF16 only)
+};
+struct GaugeRef {
+  const void* p;
+};
+
+struct Geom {
+  int V;
+  int L[4];
+  int stride[4];             // 1, Lx, Lx*Ly, Lx*Ly*Lz
+  int antiperiodic;          // time direction
+};
+
+template <typename H> struct HalfOps;
+template <> struct HalfOps<__half> {
+  static __device__ __forceinline__ float2 to2(uint32_t w) {
+    __half2 h = *reinterpret_cast<__half2*>(&w); return __half22float2(h);
+  }
+  static __device__ __forceinline__ uint32_t from2(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b); return *reinterpret_cast<uint32_t*>(&h);
+  }
+};
+template <> struct HalfOps<__nv_bfloat16> {
+  static __device__ __forceinline__ float2 to2(uint32_t w) {
+    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w); return __bfloat1622float2(h);
+  }
+  static __device__ __forceinline__ uint32_t from2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b); return *reinterpret_cast<uint32_t*>(&h);
+  }
+};
+
+template <SStore S> struct SpinorTraits;
+template <> struct SpinorTraits<SStore::F64> { using half_t = void; };
+template <> struct SpinorTraits<SStore::F32> { using half_t = void; };
+template <> struct SpinorTraits<SStore::F16> { using half_t = __half; };
+template <> struct SpinorTraits<SStore::BF16> { using half_t = __nv_bfloat16; };
+
+// ----------------------------------------------------------- spinor I/O
+// RO = true: the field is read-only for the whole kernel, so loads may use
+// the non-coherent read-only path; fields a kernel also writes use RO = false.
+template <bool RO, typename W> __device__ __forceinline__ W ld(const W* p) {
+  if constexpr (RO) return __ldg(p); else return *p;
+}
+
+template <SStore S, typename T, bool RO = true>
+__device__ __forceinline__ void load_spinor(const SpinorRef& f, int V, int s, cplx<T> v[12]) {
+  if constexpr (S == SStore::F64) {
+    const double2* p = static_cast<const double2*>(f.p);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) { double2 w = ld<RO>(p + (size_t)c * V + s); v[c] = {(T)w.x, (T)w.y}; }
+  } else if constexpr (S == SStore::F32) {
+    const float4* p = static_cast<const float4*>(f.p);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float4 w = ld<RO>(p + (size_t)k * V + s);
+      v[2 * k] = {(T)w.x, (T)w.y}; v[2 * k + 1] = {(T)w.z, (T)w.w};
+    }
+  } else {
+    using H = typename SpinorTraits<S>::half_t;
+    const uint4* p = static_cast<const uint4*>(f.p);
+    const float nrm = ld<RO>(f.norm + s);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 w = ld<RO>(p + (size_t)k * V + s);
+      float2 a = HalfOps<H>::to2(w.x), b = HalfOps<H>::to2(w.y), c = HalfOps<H>::to2(w.z), d = HalfOps<H>::to2(w.w);
+      v[4 * k + 0] = {(T)(a.x * nrm), (T)(a.y * nrm)};
+      v[4 * k + 1] = {(T)(b.x * nrm), (T)(b.y * nrm)};
+      v[4 * k + 2] = {(T)(c.x * nrm), (T)(c.y * nrm)};
+      v[4 * k + 3] = {(T)(d.x * nrm), (T)(d.y * nrm)};
+    }
+  }
+}
+
+template <SStore S, typename T>
+__device__ __forceinline__ void store_spinor(const SpinorRef& f, int V, int s, const cplx<T> v[12]) {
+  if constexpr (S == SStore::F64) {
+    double2* p = static_cast<double2*>(f.p);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) p[(size_t)c * V + s] = make_double2((double)v[c].re, (double)v[c].im);
+  } else if constexpr (S == SStore::F32) {
+    float4* p = static_cast<float4*>(f.p);
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      p[(size_t)k * V + s] = make_float4((float)v[2 * k].re, (float)v[2 * k].im, (float)v[2 * k + 1].re, (float)v[2 * k + 1].im);
+  } else {
+    using H = typename SpinorTraits<S>::half_t;
+    uint4* p = static_cast<uint4*>(f.p);
+    float m = 0.f;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) m = fmaxf(m, fmaxf(fabsf((float)v[c].re), fabsf((float)v[c].im)));
+    const float inv = m > 0.f ? 1.0f / m : 0.f;
+    f.norm[s] = m;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 w;
+      w.x = HalfOps<H>::from2((float)v[4 * k + 0].re * inv, (float)v[4 * k + 0].im * inv);
+      w.y = HalfOps<H>::from2((float)v[4 * k + 1].re * inv, (float)v[4 * k + 1].im * inv);
+      w.z = HalfOps<H>::from2((float)v[4 * k + 2].re * inv, (float)v[4 * k + 2].im * inv);
+      w.w = HalfOps<H>::from2((float)v[4 * k + 3].re * inv, (float)v[4 * k + 3].im * inv);
+      p[(size_t)k * V + s] = w;
+    }
+  }
+}
+
+// ------------------------------------------------------------- gauge I/O
+template <GStore G> struct GaugeTraits;
+template <> struct GaugeTraits<GStore::F64_18> { using half_t = void; };
+template <> struct GaugeTraits<GStore::F32_18> { using half_t = void; };
+template <> struct GaugeTraits<GStore::F32_12> { using half_t = void; };
+template <> struct GaugeTraits<GStore::F16_12> { using half_t = __half; };
+template <> struct GaugeTraits<GStore::BF16_12> { using half_t = __nv_bfloat16; };
+
+template <typename T>
+__device__ __forceinline__ void reconstruct_row2(cplx<T> u[9]) {
+  u[6] = conjg(cmul(u[1], u[5]) - cmul(u[2], u[4]));
+  u[7] = conjg(cmul(u[2], u[3]) - cmul(u[0], u[5]));
+  u[8] = conjg(cmul(u[0], u[4]) - cmul(u[1], u[3]));
+}
+
+template <GStore G, typename T>
+__device__ __forceinline__ void load_link(const GaugeRef& g, int V, int mu, int s, cplx<T> u[9]) {
+  if constexpr (G == GStore::F64_18) {
+    const double2* p = static_cast<const double2*>(g.p) + (size_t)mu * 9 * V;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) { double2 w = __ldg(p + (size_t)c * V + s); u[c] = {(T)w.x, (T)w.y}; }
+  } else if constexpr (G == GStore::F32_18) {
+    const float2* p = static_cast<const float2*>(g.p) + (size_t)mu * 9 * V;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) { float2 w = __ldg(p + (size_t)c * V + s); u[c] = {(T)w.x, (T)w.y}; }
+  } else if constexpr (G == GStore::F32_12) {
+    const float4* p = static_cast<const float4*>(g.p) + (size_t)mu * 3 * V;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float4 w = __ldg(p + (size_t)k * V + s);
+      u[2 * k] = {(T)w.x, (T)w.y}; u[2 * k + 1] = {(T)w.z, (T)w.w};
+    }
+    reconstruct_row2(u);
+  } else {
+    using H = typename GaugeTraits<G>::half_t;
+    const uint2* p = static_cast<const uint2*>(g.p) + (size_t)mu * 3 * V;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint2 w = __ldg(p + (size_t)k * V + s);
+      float2 a = HalfOps<H>::to2(w.x), b = HalfOps<H>::to2(w.y);
+      u[2 * k] = {(T)a.x, (T)a.y}; u[2 * k + 1] = {(T)b.x, (T)b.y};
+    }
+    reconstruct_row2(u);
+  }
+}
+
+// ----------------------------------------------------- spin projection
+// Projector (1 + S gamma_mu) in the DeGrand-Rossi basis.  The projected
+// spinor has rank 2: components 0, 1 ("h0", "h1") determine 2, 3.
+//   mu=x: h0 = p0 + S i p3, h1 = p1 + S i p2, c2 = -S i h1, c3 = -S i h0
+//   mu=y: h0 = p0 - S p3,   h1 = p1 + S p2,   c2 =  S h1,   c3 = -S h0
+//   mu=z: h0 = p0 + S i p2, h1 = p1 - S i p3, c2 = -S i h0, c3 =  S i h1
+//   mu=t: h0 = p0 + S p2,   h1 = p1 + S p3,   c2 =  S h0,   c3 =  S h1
+template <int MU, int S, typename T>
+__device__ __forceinline__ void project(const cplx<T> p[12], cplx<T> h0[3], cplx<T> h1[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cplx<T> p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
+    if constexpr (MU == 0) {
+      h0[c] = S > 0 ? p0 + times_i(p3) : p0 - times_i(p3);
+      h1[c] = S > 0 ? p1 + times_i(p2) : p1 - times_i(p2);
+    } else if constexpr (MU == 1) {
+      h0[c] = S > 0 ? p0 - p3 : p0 + p3;
+      h1[c] = S > 0 ? p1 + p2 : p1 - p2;
+    } else if constexpr (MU == 2) {
+      h0[c] = S > 0 ? p0 + times_i(p2) : p0 - times_i(p2);
+      h1[c] = S > 0 ? p1 - times_i(p3) : p1 + times_i(p3);
+    } else {
+      h0[c] = S > 0 ? p0 + p2 : p0 - p2;
+      h1[c] = S > 0 ? p1 + p3 : p1 - p3;
+    }
+  }
+}
+
+template <int MU, int S, typename T>
+__device__ __forceinline__ void accumulate(cplx<T> acc[12], const cplx<T> w0[3], const cplx<T> w1[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[c] = acc[c] + w0[c];
+    acc[3 + c] = acc[3 + c] + w1[c];
+    if constexpr (MU == 0) {
+      if (S > 0) { acc[6 + c] = acc[6 + c] - times_i(w1[c]); acc[9 + c] = acc[9 + c] - times_i(w0[c]); }
+      else       { acc[6 + c] = acc[6 + c] + times_i(w1[c]); acc[9 + c] = acc[9 + c] + times_i(w0[c]); }
+    } else if constexpr (MU == 1) {
+      if (S > 0) { acc[6 + c] = acc[6 + c] + w1[c]; acc[9 + c] = acc[9 + c] - w0[c]; }
+      else       { acc[6 + c] = acc[6 + c] - w1[c]; acc[9 + c] = acc[9 + c] + w0[c]; }
+    } else if constexpr (MU == 2) {
+      if (S > 0) { acc[6 + c] = acc[6 + c] - times_i(w0[c]); acc[9 + c] = acc[9 + c] + times_i(w1[c]); }
+      else       { acc[6 + c] = acc[6 + c] + times_i(w0[c]); acc[9 + c] = acc[9 + c] - times_i(w1[c]); }
+    } else {
+      if (S > 0) { acc[6 + c] = acc[6 + c] + w0[c]; acc[9 + c] = acc[9 + c] + w1[c]; }
+      else       { acc[6 + c] = acc[6 + c] - w0[c]; acc[9 + c] = acc[9 + c] - w1[c]; }
+    }
+  }
+}
+
+// w = U h   and   w = U^dag h
+template <typename T>
+__device__ __forceinline__ void su3_mul(const cplx<T> u[9], const cplx<T> h[3], cplx<T> w[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    cplx<T> a = cmul(u[3 * i], h[0]);
+    a = cmadd(a, u[3 * i + 1], h[1]);
+    w[i] = cmadd(a, u[3 * i + 2], h[2]);
+  }
+}
+template <typename T>
+__device__ __forceinline__ void su3_dagmul(const cplx<T> u[9], const cplx<T> h[3], cplx<T> w[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    cplx<T> a = cjmul(u[i], h[0]);
+    a = cjmadd(a, u[3 + i], h[1]);
+    w[i] = cjmadd(a, u[6 + i], h[2]);
+  }
+}
+
+// --------------------------------------------------- grid reductions
+// Every reducing kernel adds up to NRED doubles per thread.  Each block
+// reduces them (warp shuffles, then shared memory) and writes one partial
+// per quantity; the last block to finish (atomic ticket) sums the partials
+// in a fixed order, so the result does not depend on block scheduling,
+// and hands them to a finaliser that runs in one thread.
+struct ReduceScratch {
+  double* partials;          // [NRED][max_blocks]
+  unsigned int* ticket;      // one counter per reduction slot, left at 0
+  int max_blocks;
+};
+
+template <int NRED>
+__device__ __forceinline__ void block_sum(double (&v)[NRED], double* sh /* [NRED][32] */) {
+#pragma unroll
+  for (int q = 0; q < NRED; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) sh[q * 32 + warp] = v[q];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) {
+      double x = lane < nw ? sh[q * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      v[q] = x;               // valid in warp 0
+    }
+  }
+}
+
+// Returns true in thread 0 of the last block, with the grid totals in tot.
+template <int NRED>
+__device__ bool grid_sum(double (&v)[NRED], const ReduceScratch& rs, double (&tot)[NRED]) {
+  __shared__ double sh[NRED * 32];
+  __shared__ bool last;
+  block_sum<NRED>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) rs.partials[(size_t)q * rs.max_blocks + blockIdx.x] = v[q];
+    __threadfence();
+    unsigned int t = atomicAdd(rs.ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double w[NRED];
+#pragma unroll
+  for (int q = 0; q < NRED; ++q) {
+    double x = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      x += __ldcg(rs.partials + (size_t)q * rs.max_blocks + b);
+    w[q] = x;
+  }
+  __syncthreads();
+  block_sum<NRED>(w, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) tot[q] = w[q];
+    *rs.ticket = 0u;
+    return true;
+  }
+  return false;
+}
+
+// ------------------------------------------------------------ geometry
+__device__ __forceinline__ void site_coords(const Geom& g, int s, int c[4]) {
+  c[0] = s % g.L[0];
+  int r = s / g.L[0];
+  c[1] = r % g.L[1];
+  r /= g.L[1];
+  c[2] = r % g.L[2];
+  c[3] = r / g.L[2];
+}
+__device__ __forceinline__ int nbr_fwd(const Geom& g, int s, const int c[4], int mu) {
+  return c[mu] == g.L[mu] - 1 ? s - (g.L[mu] - 1) * g.stride[mu] : s + g.stride[mu];
+}
+__device__ __forceinline__ int nbr_bwd(const Geom& g, int s, const int c[4], int mu) {
+  return c[mu] == 0 ? s + (g.L[mu] - 1) * g.stride[mu] : s - g.stride[mu];
+}
+
+}  // namespace lq

@@ -1,0 +1,258 @@
+// Wilson hopping stencil with fused epilogues (paper Sec. 3, kernel 1: the
+// Dirac operator and its adjoint applied to the pseudofermion field inside
+// the conjugate-gradient routine; Eq. 4 gives the operator M = D + m).
+//
+//   (H psi)(x) = sum_mu [ (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu) ]
+//   M psi = psi - kappa H psi,     M^dag: projector signs of the two hops swapped
+//
+// One thread per site.  Each of the 8 hops loads the neighbour spinor,
+// projects it to two colour vectors with (1 -+ g_mu), multiplies them by
+// the link (or its adjoint), and adds the rebuilt four-spinor to a
+// register accumulator.  The neighbour indices are computed from the site
+// coordinates, no neighbour table is stored (paper Sec. 3).  What happens
+// to the result is an epilogue functor, so the CG vector updates and the
+// FP64 norms fuse into the same pass over the lattice.
+#pragma once
+#include "lq_device.cuh"
+
+namespace lq {
+
+// Device-resident scalars of one CG solve.  Kernels of an iteration read
+// alpha / beta from here and the last block of a reducing kernel updates
+// them, so an iteration needs no host round trip.
+struct SolverState {
+  double rr;          // |r|^2 of the iterated residual
+  double rr_prev;     // |r|^2 of the previous iteration
+  double tt;          // |M p|^2 = p^dag M^dag M p
+  double alpha, beta;
+  double phi2;        // |phi|^2
+  double stop2;       // tol^2 |phi|^2
+  double rr_ref;      // |r|^2 right after the last reliable update
+  double delta2;      // reliable update when rr < delta2 * rr_ref
+  double rr_true;     // |phi - M^dag M x|^2 of the last true-residual pass
+  int iter;           // iterations done
+  int iter_since_ru;  // iterations since the last reliable update
+  int ru_every;       // reliable update at least this often (0: never)
+  int maxiter;
+  int halt;           // 1: the iteration kernels return at once
+  int breakdown;      // 1: non-positive or non-finite p^dag A p, or a NaN
+  int hist_len;       // capacity of hist
+  int pad_;
+  double* hist;       // relative iterated residual per iteration (may be null)
+};
+
+struct NoEpiState {};
+
+template <int MU, bool DAG, GStore G, SStore SI, typename T>
+__device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, const SpinorRef& in, int s,
+                                        const int c[4], cplx<T> acc[12]) {
+  constexpr int SF = DAG ? +1 : -1;   // forward hop uses (1 + SF g_mu)
+  {
+    const int n = nbr_fwd(geo, s, c, MU);
+    cplx<T> p[12];
+    load_spinor<SI, T>(in, geo.V, n, p);
+    cplx<T> h0[3], h1[3];
+    project<MU, SF>(p, h0, h1);
+    if (MU == 3 && geo.antiperiodic && c[3] == geo.L[3] - 1) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { h0[k] = -h0[k]; h1[k] = -h1[k]; }
+    }
+    cplx<T> u[9];
+    load_link<G, T>(U, geo.V, MU, s, u);
+    cplx<T> w0[3], w1[3];
+    su3_mul(u, h0, w0);
+    su3_mul(u, h1, w1);
+    accumulate<MU, SF>(acc, w0, w1);
+  }
+  {
+    const int n = nbr_bwd(geo, s, c, MU);
+    cplx<T> p[12];
+    load_spinor<SI, T>(in, geo.V, n, p);
+    cplx<T> h0[3], h1[3];
+    project<MU, -SF>(p, h0, h1);
+    if (MU == 3 && geo.antiperiodic && c[3] == 0) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { h0[k] = -h0[k]; h1[k] = -h1[k]; }
+    }
+    cplx<T> u[9];
+    load_link<G, T>(U, geo.V, MU, n, u);
+    cplx<T> w0[3], w1[3];
+    su3_dagmul(u, h0, w0);
+    su3_dagmul(u, h1, w1);
+    accumulate<MU, -SF>(acc, w0, w1);
+  }
+}
+
+template <typename T, GStore G, SStore SI, bool DAG, class Epi>
+__global__ void __launch_bounds__(256) dslash_kernel(Geom geo, GaugeRef U, SpinorRef in, T kappa, Epi epi,
+                                                      ReduceScratch rs) {
+  if (epi.halted()) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  double red[Epi::NRED];
+#pragma unroll
+  for (int q = 0; q < Epi::NRED; ++q) red[q] = 0.0;
+  if (s < geo.V) {
+    int c[4];
+    site_coords(geo, s, c);
+    cplx<T> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = {(T)0, (T)0};
+    hop_dir<0, DAG, G, SI, T>(geo, U, in, s, c, acc);
+    hop_dir<1, DAG, G, SI, T>(geo, U, in, s, c, acc);
+    hop_dir<2, DAG, G, SI, T>(geo, U, in, s, c, acc);
+    hop_dir<3, DAG, G, SI, T>(geo, U, in, s, c, acc);
+    cplx<T> ctr[12];
+    load_spinor<SI, T>(in, geo.V, s, ctr);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      acc[k].re = fma(-kappa, acc[k].re, ctr[k].re);
+      acc[k].im = fma(-kappa, acc[k].im, ctr[k].im);
+    }
+    epi.apply(geo.V, s, acc, red);
+  }
+  if constexpr (Epi::REDUCE) {
+    double tot[Epi::NRED];
+    if (grid_sum<Epi::NRED>(red, rs, tot)) epi.finalize(tot);
+  }
+}
+
+// ------------------------------------------------------------ epilogues
+template <SStore SO>
+struct EpiStore {                       // out = M psi
+  static constexpr int NRED = 1;
+  static constexpr bool REDUCE = false;
+  SpinorRef out;
+  __device__ bool halted() const { return false; }
+  template <typename T> __device__ void apply(int V, int s, cplx<T> v[12], double (&)[NRED]) const {
+    store_spinor<SO, T>(out, V, s, v);
+  }
+  __device__ void finalize(double (&)[NRED]) const {}
+};
+
+template <SStore SO>
+struct EpiStoreNorm {                   // out = M psi, *result = |out|^2
+  static constexpr int NRED = 1;
+  static constexpr bool REDUCE = true;
+  SpinorRef out;
+  double* result;
+  __device__ bool halted() const { return false; }
+  template <typename T> __device__ void apply(int V, int s, cplx<T> v[12], double (&red)[NRED]) const {
+    store_spinor<SO, T>(out, V, s, v);
+    double a = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) a += (double)v[k].re * (double)v[k].re + (double)v[k].im * (double)v[k].im;
+    red[0] += a;
+  }
+  __device__ void finalize(double (&tot)[NRED]) const { *result = tot[0]; }
+};
+
+// CG step 1:  t = M p, tt = |t|^2, alpha = rr / tt
+template <SStore ST>
+struct EpiCG1 {
+  static constexpr int NRED = 1;
+  static constexpr bool REDUCE = true;
+  SpinorRef t;
+  SolverState* st;
+  __device__ bool halted() const { return *(volatile const int*)&st->halt; }
+  template <typename T> __device__ void apply(int V, int s, cplx<T> v[12], double (&red)[NRED]) const {
+    store_spinor<ST, T>(t, V, s, v);
+    double a = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) a += (double)v[k].re * (double)v[k].re + (double)v[k].im * (double)v[k].im;
+    red[0] += a;
+  }
+  __device__ void finalize(double (&tot)[NRED]) const {
+    const double tt = tot[0];
+    st->tt = tt;
+    if (!(tt > 0.0) || !isfinite(tt) || !isfinite(st->rr)) {
+      st->breakdown = 1;
+      st->halt = 1;
+      st->alpha = 0.0;
+    } else {
+      st->alpha = st->rr / tt;
+    }
+  }
+};
+
+// CG step 2:  r <- r - alpha M^dag t,  x <- x + alpha p,  rr_new = |r|^2,
+// beta = rr_new / rr; decides whether the iteration halts (converged
+// estimate, reliable update due, or iteration limit).
+template <SStore SR, SStore SX, SStore SP>
+struct EpiCG2 {
+  static constexpr int NRED = 1;
+  static constexpr bool REDUCE = true;
+  SpinorRef r, x, p;
+  SolverState* st;
+  __device__ bool halted() const { return *(volatile const int*)&st->halt; }
+  template <typename T> __device__ void apply(int V, int s, cplx<T> v[12], double (&red)[NRED]) const {
+    const T alpha = (T)st->alpha;
+    cplx<T> rv[12], xv[12], pv[12];
+    load_spinor<SR, T, false>(r, V, s, rv);
+    load_spinor<SX, T, false>(x, V, s, xv);
+    load_spinor<SP, T>(p, V, s, pv);
+    double a = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      rv[k].re = fma(-alpha, v[k].re, rv[k].re);
+      rv[k].im = fma(-alpha, v[k].im, rv[k].im);
+      xv[k].re = fma(alpha, pv[k].re, xv[k].re);
+      xv[k].im = fma(alpha, pv[k].im, xv[k].im);
+      a += (double)rv[k].re * (double)rv[k].re + (double)rv[k].im * (double)rv[k].im;
+    }
+    store_spinor<SR, T>(r, V, s, rv);
+    store_spinor<SX, T>(x, V, s, xv);
+    red[0] += a;
+  }
+  __device__ void finalize(double (&tot)[NRED]) const {
+    const double rr_new = tot[0];
+    const int it = st->iter;
+    if (st->hist != nullptr && it < st->hist_len) st->hist[it] = sqrt(rr_new / st->phi2);
+    st->iter = it + 1;
+    st->iter_since_ru += 1;
+    st->beta = rr_new / st->rr;
+    st->rr_prev = st->rr;
+    st->rr = rr_new;
+    if (!isfinite(rr_new)) { st->breakdown = 1; st->halt = 1; return; }
+    if (rr_new <= st->stop2) st->halt = 1;
+    if (st->ru_every > 0 && st->iter_since_ru >= st->ru_every) st->halt = 1;
+    if (st->delta2 > 0.0 && rr_new < st->delta2 * st->rr_ref) st->halt = 1;
+    if (st->iter >= st->maxiter) st->halt = 1;
+  }
+};
+
+// True residual in FP64:  v = M^dag (M x)  ->  r = phi - v, |r|^2.
+// Optionally also stores r in a low-precision field (reliable update).
+template <SStore SLO, bool STORE_LO>
+struct EpiResidual {
+  static constexpr int NRED = 1;
+  static constexpr bool REDUCE = true;
+  SpinorRef phi, r, r_lo;
+  SolverState* st;
+  __device__ bool halted() const { return false; }
+  template <typename T> __device__ void apply(int V, int s, cplx<T> v[12], double (&red)[NRED]) const {
+    cplx<double> ph[12];
+    load_spinor<SStore::F64, double>(phi, V, s, ph);
+    cplx<double> rv[12];
+    double a = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      rv[k] = {ph[k].re - (double)v[k].re, ph[k].im - (double)v[k].im};
+      a += rv[k].re * rv[k].re + rv[k].im * rv[k].im;
+    }
+    store_spinor<SStore::F64, double>(r, V, s, rv);
+    if constexpr (STORE_LO) store_spinor<SLO, double>(r_lo, V, s, rv);
+    red[0] += a;
+  }
+  __device__ void finalize(double (&tot)[NRED]) const { st->rr_true = tot[0]; }
+};
+
+inline int grid_for(int V, int bs) { return (V + bs - 1) / bs; }
+
+template <typename T, GStore G, SStore SI, bool DAG, class Epi>
+inline void launch_dslash(const Geom& geo, GaugeRef U, SpinorRef in, double kappa, const Epi& epi,
+                          const ReduceScratch& rs, cudaStream_t stream) {
+  const int bs = 256;
+  dslash_kernel<T, G, SI, DAG, Epi><<<grid_for(geo.V, bs), bs, 0, stream>>>(geo, U, in, (T)kappa, epi, rs);
+}
+
+}  // namespace lq

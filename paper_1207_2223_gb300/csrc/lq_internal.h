@@ -1,0 +1,118 @@
+// Host-side internals shared by the translation units of the library:
+// the context object and the kernel launchers each unit provides.
+#pragma once
+#include <cuda_runtime.h>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "lq_device.cuh"
+#include "lq_dslash.cuh"
+#include "../../include/lq.h"
+
+namespace lq {
+
+constexpr int kNumPrec = 5;   // LQ_F64 .. LQ_BF16_12
+
+inline GStore gauge_store_of(int prec) {
+  switch (prec) {
+    case LQ_F64: return GStore::F64_18;
+    case LQ_F32: return GStore::F32_18;
+    case LQ_F32_12: return GStore::F32_12;
+    case LQ_F16_12: return GStore::F16_12;
+    default: return GStore::BF16_12;
+  }
+}
+inline SStore spinor_store_of(int prec) {
+  switch (prec) {
+    case LQ_F64: return SStore::F64;
+    case LQ_F32: case LQ_F32_12: return SStore::F32;
+    case LQ_F16_12: return SStore::F16;
+    default: return SStore::BF16;
+  }
+}
+size_t spinor_bytes(SStore s, int V);        // chunk array only
+size_t gauge_bytes(GStore g, int V);
+
+// A spinor field in one storage format, owned by the context.
+struct Field {
+  SStore store = SStore::F64;
+  void* data = nullptr;
+  float* norm = nullptr;
+  SpinorRef ref() const { return SpinorRef{data, norm}; }
+};
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace lq
+
+struct lq_ctx {
+  lq::Geom geo{};
+  int device = 0;
+  cudaStream_t stream = nullptr;         // work stream (the caller's)
+  cudaStream_t capture_stream = nullptr; // private stream used only to record graphs
+  std::string last_error;
+
+  // gauge field: FP64 master copy and lazily built low-precision copies
+  void* gauge64 = nullptr;
+  void* gauge_lo[lq::kNumPrec] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool gauge_lo_valid[lq::kNumPrec] = {false, false, false, false, false};
+  bool gauge_set = false;
+
+  // canonical-layout staging buffers (device)
+  double* stage_in = nullptr;            // V * 24 doubles
+  double* stage_out = nullptr;           // V * 24 doubles
+  double* stage_gauge = nullptr;         // V * 72 doubles
+
+  // FP64 solver fields
+  lq::Field phi64, x64, r64, p64, t64, tmp64;
+  // low-precision solver fields, one set per storage format
+  lq::Field r_lo[4], p_lo[4], t_lo[4], x_lo[4];
+
+  // reductions and solver scalars
+  lq::ReduceScratch rs{};
+  lq::SolverState* state = nullptr;      // device
+  lq::SolverState* state_host = nullptr; // pinned mirror
+  double* dscalar = nullptr;             // device scratch scalars [8]
+  double* dscalar_host = nullptr;        // pinned mirror [8]
+
+  std::map<std::tuple<int, int, int, double>, lq::GraphEntry> graphs;
+};
+
+namespace lq {
+
+// ---- layout (k_layout.cu)
+void launch_pack_gauge64(const Geom& g, const double* canon, void* soa, cudaStream_t st);
+void launch_unpack_gauge64(const Geom& g, const void* soa, double* canon, cudaStream_t st);
+void launch_convert_gauge(const Geom& g, const void* soa64, GStore dst, void* out, cudaStream_t st);
+void launch_pack_spinor(const Geom& g, const double* canon, SStore s, SpinorRef out, cudaStream_t st);
+void launch_unpack_spinor(const Geom& g, SStore s, SpinorRef in, double* canon, cudaStream_t st);
+
+// ---- BLAS-1 (k_blas.cu)
+// phi2 = |phi|^2 -> state; x = 0; r = phi; p = phi (each in its own format)
+void launch_solver_init(const Geom& g, SpinorRef phi64, SStore sx, SpinorRef x, SStore sr, SpinorRef r,
+                        SStore sp, SpinorRef p, SolverState* st, const ReduceScratch& rs, cudaStream_t stream);
+// p = r + beta p (skipped when halted unless forced)
+void launch_xpay_p(const Geom& g, SStore s, SpinorRef r, SpinorRef p, SolverState* st, bool forced,
+                   cudaStream_t stream);
+// x_hi += x_lo ; x_lo = 0
+void launch_accumulate_x(const Geom& g, SStore slo, SpinorRef xlo, SpinorRef xhi, cudaStream_t stream);
+// after a true-residual pass: beta = rr_true / rr_prev (0 when restart), rr = rr_ref = rr_true, resume
+void launch_state_after_residual(SolverState* st, int restart, cudaStream_t stream);
+void launch_zero_spinor(const Geom& g, SStore s, SpinorRef f, cudaStream_t stream);
+
+// ---- Wilson operator applications (k_apply.cu): out = M in or M^dag in
+void apply_M_prec(const Geom& g, int prec, const void* gauge, SpinorRef in, SpinorRef out, double kappa,
+                  bool dagger, cudaStream_t stream);
+
+// ---- FP64 CG pieces (k_cg64.cu)
+void cg64_iteration(lq_ctx* c, double kappa, cudaStream_t stream);
+void cg64_true_residual(lq_ctx* c, double kappa, int store_lo_prec, cudaStream_t stream);
+
+// ---- low-precision CG iteration (k_cglo.cu)
+void cglo_iteration(lq_ctx* c, int prec, double kappa, cudaStream_t stream);
+
+}  // namespace lq

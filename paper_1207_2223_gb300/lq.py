@@ -1,0 +1,169 @@
+"""ctypes binding of the C interface in include/lq.h (argument marshalling only).
+
+Buffers may be torch tensors (CUDA or CPU) or numpy arrays; their data
+pointers go straight to the library, which stages host buffers itself.
+Complex fields use the canonical layouts of lq.h:
+  gauge  complex128 (V, 4, 3, 3)   spinor complex128 (V, 4, 3)
+  momentum / force float64 (V, 4, 8)
+Every non-zero status raises LQError with the library's message.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblq.so")
+
+LQ_OK, LQ_ERR_ARG, LQ_ERR_SHAPE, LQ_ERR_CUDA, LQ_ERR_NOT_CONVERGED, LQ_ERR_NAN, LQ_ERR_STATE = range(7)
+LQ_F64, LQ_F32, LQ_F32_12, LQ_F16_12, LQ_BF16_12 = range(5)
+PRECISIONS = {"f64": LQ_F64, "f32": LQ_F32, "f32_12": LQ_F32_12, "f16_12": LQ_F16_12, "bf16_12": LQ_BF16_12}
+
+
+class LQError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("lq status %d: %s" % (status, msg))
+        self.status = status
+
+
+class lq_solve_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("converged", ctypes.c_int), ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+
+# name -> (restype, argtypes); the C declarations are in include/lq.h
+SIGNATURES = {
+    "lq_version": (ctypes.c_char_p, []),
+    "lq_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_I), _I, _P]),
+    "lq_destroy": (_I, [_P]),
+    "lq_last_error": (ctypes.c_char_p, [_P]),
+    "lq_set_stream": (_I, [_P, _P]),
+    "lq_volume": (ctypes.c_int64, [_P]),
+    "lq_gauge_set": (_I, [_P, _P]),
+    "lq_gauge_get": (_I, [_P, _P]),
+    "lq_apply_M": (_I, [_P, _P, _P, _D, _I, _I]),
+    "lq_apply_MdagM": (_I, [_P, _P, _P, _D, _I]),
+    "lq_solve_MdagM": (_I, [_P, _P, _P, _D, _D, _I, _I, _I, _P, _I, ctypes.POINTER(lq_solve_stats)]),
+    "lq_time_dslash": (_I, [_P, _P, _D, _I, _I, _I, _I, ctypes.POINTER(_D)]),
+}
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError("CUDA library %s not built: run paper_1207_2223_gb300.build.build()" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(buf):
+    if buf is None:
+        return None
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("buffer must be contiguous")
+        return buf.data_ptr()
+    if hasattr(buf, "ctypes"):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffer must be C-contiguous")
+        return buf.ctypes.data
+    return int(buf)
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+def _check(ctx, status):
+    if status != LQ_OK:
+        msg = load().lq_last_error(ctx)
+        raise LQError(status, msg.decode() if msg else "")
+
+
+def lq_version():
+    return load().lq_version().decode()
+
+
+def lq_create(dims, t_antiperiodic=True, stream=None):
+    lib = load()
+    out = _P()
+    d = (_I * 4)(*[int(v) for v in dims])
+    st = _current_stream() if stream is None else stream
+    _check(None, lib.lq_create(ctypes.byref(out), d, 1 if t_antiperiodic else 0, st))
+    return out
+
+
+def lq_destroy(ctx):
+    _check(ctx, load().lq_destroy(ctx))
+
+
+def lq_last_error(ctx):
+    return load().lq_last_error(ctx).decode()
+
+
+def lq_set_stream(ctx, stream):
+    _check(ctx, load().lq_set_stream(ctx, stream))
+
+
+def lq_volume(ctx):
+    return int(load().lq_volume(ctx))
+
+
+def lq_gauge_set(ctx, U):
+    _check(ctx, load().lq_gauge_set(ctx, _ptr(U)))
+
+
+def lq_gauge_get(ctx, U):
+    _check(ctx, load().lq_gauge_get(ctx, _ptr(U)))
+
+
+def lq_apply_M(ctx, out, inp, kappa, dagger=False, prec=LQ_F64):
+    _check(ctx, load().lq_apply_M(ctx, _ptr(out), _ptr(inp), float(kappa), 1 if dagger else 0, int(prec)))
+
+
+def lq_apply_MdagM(ctx, out, inp, kappa, prec=LQ_F64):
+    _check(ctx, load().lq_apply_MdagM(ctx, _ptr(out), _ptr(inp), float(kappa), int(prec)))
+
+
+def lq_solve_MdagM(ctx, x, phi, kappa, tol=1e-10, maxiter=100000, inner_prec=LQ_F64, reliable_every=50,
+                   hist=None, raise_on_error=True):
+    """Returns (status, stats dict); raises on errors other than NOT_CONVERGED unless told not to."""
+    st = lq_solve_stats()
+    n = 0 if hist is None else len(hist)
+    status = load().lq_solve_MdagM(ctx, _ptr(x), _ptr(phi), float(kappa), float(tol), int(maxiter),
+                                   int(inner_prec), int(reliable_every), _ptr(hist), n, ctypes.byref(st))
+    if raise_on_error and status not in (LQ_OK, LQ_ERR_NOT_CONVERGED):
+        _check(ctx, status)
+    return status, st.as_dict()
+
+
+def lq_time_dslash(ctx, inp, kappa, dagger=False, prec=LQ_F64, n=20, flush_l2=False):
+    """Average device milliseconds of one application of M (or M^dag)."""
+    ms = _D()
+    _check(ctx, load().lq_time_dslash(ctx, _ptr(inp), float(kappa), 1 if dagger else 0, int(prec), int(n),
+                                      1 if flush_l2 else 0, ctypes.byref(ms)))
+    return ms.value
+
+
+__all__ = [n for n in list(globals()) if n.startswith(("lq_", "LQ_"))] + ["LQError", "PRECISIONS", "load"]

@@ -1,0 +1,49 @@
+"""The C library loads without a GPU and exports every entry point include/lq.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "lq.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(lq_\w+)\s*\(", txt, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1207_2223_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_functions():
+    names = declared_functions()
+    assert "lq_create" in names and "lq_solve_MdagM" in names
+    assert len(names) >= 10
+
+
+def test_every_declared_symbol_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declaration():
+    from paper_1207_2223_gb300 import lq
+    assert set(declared_functions()) == set(lq.SIGNATURES)
+
+
+def test_version_without_gpu(lib):
+    lib.lq_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.lq_version()
+
+
+def test_create_rejects_bad_shape_without_gpu(lib):
+    out = ctypes.c_void_p()
+    dims = (ctypes.c_int * 4)(1, 4, 4, 4)
+    assert lib.lq_create(ctypes.byref(out), dims, 1, None) == 2      # LQ_ERR_SHAPE
+    assert not out.value

@@ -1,0 +1,107 @@
+"""CG on M^dag M (Sec. 1 after Eq. 3; Sec. 3) on the GPU against the oracle's solve."""
+import numpy as np
+import pytest
+
+from oracle.cg import cg_MdagM
+from synth import Lattice, gauge_exp_iA, source
+from tests.gpu_common import require_gpu, dev, host, rel_err, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lq():
+    return require_gpu()
+
+
+# The oracle solves to 1e-13; the GPU to 1e-10.  The solution error is at
+# most cond(M^dag M) times the residual; cond stays below ~1e3 for these
+# lattices (CG converges in < 300 iterations), so 1e-6 is a safe bound.
+X_TOL = 1e-6
+
+
+@pytest.mark.parametrize("dims,kappa,sigma", [((4, 4, 4, 4), 0.15, 0.3), ((6, 4, 2, 6), 0.155, 0.3),
+                                              ((8, 8, 8, 8), 0.156, 0.25)])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
+def test_solve_matches_oracle(lq, dims, kappa, sigma, prec):
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, sigma, 2)
+    phi = source(lat, 7)
+    ohist = []
+    x_ref, it_ref, res_ref = cg_MdagM(U, phi, dims, kappa, tol=1e-13, history=ohist)
+    # iterations the oracle's recursion needed to reach 1e-10
+    it_ref10 = 1 + int(np.argmax(np.array(ohist) <= 1e-10))
+    ctx = lq.lq_create(dims)
+    try:
+        lq.lq_gauge_set(ctx, dev(U))
+        x = torch.zeros_like(dev(phi))
+        hist = np.zeros(5000)
+        status, st = lq.lq_solve_MdagM(ctx, x, dev(phi), kappa, 1e-10, 5000, prec, 50, hist=hist)
+        got = host(x)
+        # residual recomputed independently through the FP64 operator
+        r = torch.empty_like(x)
+        lq.lq_apply_MdagM(ctx, r, x, kappa, lq.LQ_F64)
+        res = np.linalg.norm(phi - host(r)) / np.linalg.norm(phi)
+    finally:
+        lq.lq_destroy(ctx)
+    assert status == lq.LQ_OK and st["converged"] == 1
+    assert st["true_rel_resid"] <= 1e-10 and res <= 1e-10
+    assert rel_err(got, x_ref) < X_TOL
+    n = st["iterations"]
+    assert n > 0 and np.all(hist[:n] > 0)
+    if prec == 0:
+        # same algorithm and stopping rule: the iteration count agrees up to rounding drift
+        assert abs(n - it_ref10) <= max(3, it_ref10 // 20), (n, it_ref10)
+
+
+def test_zero_source_and_errors(lq):
+    dims = (4, 4, 4, 4)
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, 0.3, 1)
+    ctx = lq.lq_create(dims)
+    try:
+        x = torch.ones((lat.V, 4, 3), dtype=torch.complex128, device="cuda")
+        with pytest.raises(lq.LQError) as e:
+            lq.lq_solve_MdagM(ctx, x, torch.zeros_like(x), 0.15)
+        assert e.value.status == lq.LQ_ERR_STATE         # no gauge field yet
+        lq.lq_gauge_set(ctx, dev(U))
+        status, st = lq.lq_solve_MdagM(ctx, x, torch.zeros_like(x), 0.15)
+        assert status == lq.LQ_OK and st["iterations"] == 0
+        assert float(x.abs().max()) == 0.0
+        phi = dev(source(lat, 3))
+        status, st = lq.lq_solve_MdagM(ctx, x, phi, 0.15, 1e-10, 5)
+        assert status == lq.LQ_ERR_NOT_CONVERGED and st["iterations"] == 5 and st["true_rel_resid"] > 1e-10
+        bad = phi.clone()
+        bad[3, 1, 2] = complex(float("nan"), 0.0)
+        with pytest.raises(lq.LQError) as e:
+            lq.lq_solve_MdagM(ctx, x, bad, 0.15)
+        assert e.value.status == lq.LQ_ERR_NAN
+        with pytest.raises(lq.LQError):
+            lq.lq_solve_MdagM(ctx, x, phi, 0.15, -1.0)
+    finally:
+        lq.lq_destroy(ctx)
+
+
+def test_full_size_mixed_and_f64_solves(lq):
+    """32^3 x 64, sigma 0.25, seed 2, kappa 0.156: FP16 and FP64 solves both reach a 1e-10 FP64
+    true residual, and agree with each other within the conditioning bound."""
+    dims = (32, 32, 32, 64)
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, 0.25, 2)
+    phi = dev(source(lat, 2))
+    ctx = lq.lq_create(dims)
+    try:
+        lq.lq_gauge_set(ctx, dev(U))
+        xs = {}
+        for prec in (lq.LQ_F16_12, lq.LQ_F64):
+            x = torch.zeros_like(phi)
+            status, st = lq.lq_solve_MdagM(ctx, x, phi, 0.156, 1e-10, 20000, prec, 50)
+            assert status == lq.LQ_OK and st["true_rel_resid"] <= 1e-10, st
+            r = torch.empty_like(x)
+            lq.lq_apply_MdagM(ctx, r, x, 0.156, lq.LQ_F64)
+            assert float(torch.linalg.vector_norm(phi - r) / torch.linalg.vector_norm(phi)) <= 1e-10
+            xs[prec] = x
+        d = float(torch.linalg.vector_norm(xs[lq.LQ_F16_12] - xs[lq.LQ_F64]) / torch.linalg.vector_norm(xs[lq.LQ_F64]))
+        assert d < X_TOL
+    finally:
+        lq.lq_destroy(ctx)
