@@ -155,6 +155,34 @@ lq_status lq_solve_MdagM(lq_ctx* ctx, double* x, const double* phi, double kappa
 lq_status lq_time_dslash(lq_ctx* ctx, const double* in, double kappa, int dagger, int prec, int n, int flush_l2,
                          double* ms);
 
+/* out = M^dag M in, FP64, without allocating any device memory.
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot let a library allocate GPU memory: programs that give all device
+ * memory to their own pool allocator and forbid cudaMalloc once they are
+ * running, or plugins that live inside a host application under a fixed
+ * device-memory budget.  It needs no context (lq_create allocates): U, in
+ * and out are the caller's device buffers in the canonical layouts above
+ * (U [V][4][3][3] complex, in / out [V][4][3] complex, 16-byte aligned),
+ * dims and t_antiperiodic as in lq_create, and the work is issued on
+ * `cuda_stream` (a cudaStream_t) without synchronising.  out may equal in.
+ *
+ * The intermediate field M in is kept in one array compiled into the
+ * library (12 MiB, held on every GPU that loads the library until the
+ * process exits), so the lattice may have at most 65,536 sites (e.g. 16^4);
+ * larger lattices return LQ_ERR_SHAPE.  All calls share that array: two
+ * calls whose work overlaps on the GPU (different streams, or different
+ * host threads without ordering) race and give wrong results; calls on the
+ * same stream are ordered and safe.  Every call overwrites the whole part
+ * of the array it uses before reading it, so no state carries over.
+ * The first call on each device looks up the array's device address (one
+ * cudaGetSymbolAddress with that device current); make that first call
+ * before capturing the stream into a CUDA graph.
+ * Errors: LQ_ERR_ARG, LQ_ERR_SHAPE, LQ_ERR_CUDA; the message is returned by
+ * lq_last_error(NULL). */
+lq_status lq_apply_MdagM_static(double* out, const double* U, const double* in, const int dims[4],
+                                int t_antiperiodic, double kappa, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -154,6 +154,9 @@ lq_status read_state(lq_ctx* c) {
 
 }  // namespace
 
+// Error text of calls that run without a context (read with lq_last_error(NULL)).
+void lq_set_global_error(const std::string& msg) { g_create_error = msg; }
+
 extern "C" {
 
 const char* lq_version(void) { return "lq 0.1 (sm_103a)"; }

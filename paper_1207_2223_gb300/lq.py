@@ -51,6 +51,7 @@ SIGNATURES = {
     "lq_apply_MdagM": (_I, [_P, _P, _P, _D, _I]),
     "lq_solve_MdagM": (_I, [_P, _P, _P, _D, _D, _I, _I, _I, _P, _I, ctypes.POINTER(lq_solve_stats)]),
     "lq_time_dslash": (_I, [_P, _P, _D, _I, _I, _I, _I, ctypes.POINTER(_D)]),
+    "lq_apply_MdagM_static": (_I, [_P, _P, _P, ctypes.POINTER(_I), _I, _D, _P]),
 }
 
 _lib = None
@@ -164,6 +165,18 @@ def lq_time_dslash(ctx, inp, kappa, dagger=False, prec=LQ_F64, n=20, flush_l2=Fa
     _check(ctx, load().lq_time_dslash(ctx, _ptr(inp), float(kappa), 1 if dagger else 0, int(prec), int(n),
                                       1 if flush_l2 else 0, ctypes.byref(ms)))
     return ms.value
+
+
+def lq_apply_MdagM_static(out, U, inp, dims, kappa, t_antiperiodic=True, stream=None):
+    """out = M^dag M inp on caller device buffers, with no device allocation.
+
+    For callers that cannot let the library allocate GPU memory (all memory
+    owned by their own pool, or a fixed budget); at most 65,536 sites.
+    Asynchronous on `stream` (the current torch stream by default)."""
+    d = (_I * 4)(*[int(v) for v in dims])
+    st = _current_stream() if stream is None else stream
+    _check(None, load().lq_apply_MdagM_static(_ptr(out), _ptr(U), _ptr(inp), d, 1 if t_antiperiodic else 0,
+                                              float(kappa), st))
 
 
 __all__ = [n for n in list(globals()) if n.startswith(("lq_", "LQ_"))] + ["LQError", "PRECISIONS", "load"]
