@@ -145,6 +145,69 @@ lq_status lq_solve_MdagM(lq_ctx* ctx, double* x, const double* phi, double kappa
                          int inner_prec, int reliable_every, double* hist, int hist_len,
                          lq_solve_stats* stats);
 
+/* ---------------------------------------------------------------- MD */
+
+/* Parameters of one HMC trajectory (Sec. 3, the three steps of the evolution). */
+typedef struct {
+  double beta;          /* gauge coupling of the Wilson plaquette action */
+  double kappa;         /* hopping parameter */
+  double tau;           /* trajectory length; step eps = tau / n_steps */
+  int n_steps;          /* leapfrog steps (> 0) */
+  double tol;           /* CG tolerance of every solve (FP64 true relative residual) */
+  int maxiter;          /* CG iteration limit per solve */
+  int inner_prec;       /* lq_prec of the CG iterations (LQ_F64 or mixed) */
+  int reliable_every;   /* reliable-update interval of mixed solves */
+} lq_hmc_params;
+
+typedef struct {
+  double dH, dK, dSg, dSf;   /* H_new - H_old and its kinetic, gauge and pseudofermion parts */
+  int accepted;              /* Metropolis decision */
+  double plaquette;          /* of the configuration kept (accepted or restored) */
+  int solves;                /* CG solves in the trajectory (n_steps + 2) */
+  int64_t cg_iterations;     /* their total iterations */
+  int64_t kernel_launches;   /* kernels launched by the call */
+  double seconds;            /* host wall-clock of the call */
+} lq_traj_result;
+
+/* Average plaquette <Re tr U_P / 3> over the 6 V plaquettes (1 for U = 1);
+ * the measurement made at the end of each trajectory (Sec. 3).  Synchronises. */
+lq_status lq_plaquette(lq_ctx* ctx, double* plaq);
+
+/* Wilson gauge action S_g = beta sum_P (1 - Re tr U_P / 3) (S_g of Eq. 1, 5).
+ * Synchronises. */
+lq_status lq_gauge_action(lq_ctx* ctx, double beta, double* S);
+
+/* Gauge force F_a(x, mu) = dS_g / d omega_a under U_mu(x) -> exp(i omega_a t_a) U_mu(x),
+ * i.e. (beta/3) Im tr(t_a U_mu(x) Sigma_mu(x)) with the six staples Sigma_mu
+ * (Sec. 3 kernel 2).  F: canonical [V][4][8].  FP64. */
+lq_status lq_gauge_force(lq_ctx* ctx, double* F, double beta);
+
+/* Fermion force F_a(x, mu) = dS_f / d omega_a for S_f = phi^dag (M^dag M)^{-1} phi, given
+ * the solution X = (M^dag M)^{-1} phi (canonical spinor); Y = M X is formed inside
+ * (Sec. 3 kernel 3).  F: canonical [V][4][8].  FP64. */
+lq_status lq_fermion_force(lq_ctx* ctx, double* F, const double* X, double kappa);
+
+/* Link update U_mu(x) <- exp(i eps P_mu(x)) U_mu(x), P = sum_a p_a t_a, then
+ * reunitarisation (Gram-Schmidt rows 1, 2; row 3 = conj(row1 x row2)) (Sec. 3
+ * kernel 4; Sec. 2: U and exp(ip) conjugate).  p: canonical [V][4][8].  The
+ * context's gauge field changes. */
+lq_status lq_link_update(lq_ctx* ctx, const double* p, double eps);
+
+/* One HMC trajectory on the context's gauge field (Eq. 5; Sec. 2; Sec. 3 steps 1-3):
+ *   heat bath   p (canonical [V][4][8], su(3) coefficients N(0,1)) and chi
+ *               (canonical spinor, density exp(-chi^dag chi)) are the caller's draws;
+ *               phi = M^dag chi; S_f at the start is chi^dag chi
+ *   leapfrog    p -= eps/2 F; n_steps x (U <- exp(i eps p) U; p -= eps F), the
+ *               last momentum step eps/2; F = gauge + fermion force, every solve
+ *               from x0 = 0 to the tolerance of params
+ *   Metropolis  accept iff u < exp(-Delta H), u in [0, 1) the caller's draw;
+ *               Delta H summed from per-site differences in FP64
+ * On return p holds the momenta at the end of the leapfrog, the context holds
+ * the new links if accepted and the old ones otherwise.  A failed solve leaves
+ * the old links and returns its status.  Synchronises. */
+lq_status lq_hmc_trajectory(lq_ctx* ctx, const lq_hmc_params* params, double* p, const double* chi, double u,
+                            lq_traj_result* result);
+
 /* Measurement: apply M (dagger = 0) or M^dag (1) `n` times in precision
  * `prec` to `in` (packed once, outside the timed region) and return the
  * average device time of one application in *ms, measured with CUDA events

@@ -152,6 +152,167 @@ lq_status read_state(lq_ctx* c) {
   return LQ_OK;
 }
 
+// Solve M^dag M x = phi with phi already in c->phi64; the solution is left in
+// c->x64.  Host scalars come back once per CUDA graph of iterations.
+lq_status solve_internal(lq_ctx* c, double kappa, double tol, int maxiter, int inner, int reliable_every,
+                         double* hist_dev, int hist_len, lq_solve_stats* sout) {
+  LQ_TRY(require_gauge(c, inner));
+  LQ_TRY(ensure_solver_fields(c, inner));
+  const Geom& g = c->geo;
+  const bool mixed = inner != LQ_F64;
+  const SStore slo = spinor_store_of(inner);
+  const int k = (int)slo;
+  SolverState h{};
+  h.stop2 = tol * tol;
+  h.ru_every = mixed ? reliable_every : 0;
+  h.delta2 = mixed ? 1e-4 : 0.0;          // reliable update once |r| fell by 1e-2
+  h.maxiter = maxiter;
+  h.hist = hist_dev;
+  h.hist_len = hist_dev ? hist_len : 0;
+  *c->state_host = h;
+  LQ_CUDA(c, cudaMemcpyAsync(c->state, c->state_host, sizeof(SolverState), cudaMemcpyHostToDevice, c->stream));
+  if (mixed) {
+    launch_zero_spinor(g, SStore::F64, c->x64.ref(), c->stream);
+    launch_solver_init(g, c->phi64.ref(), slo, c->x_lo[k].ref(), slo, c->r_lo[k].ref(), slo, c->p_lo[k].ref(),
+                       c->state, c->rs, c->stream);
+  } else {
+    launch_solver_init(g, c->phi64.ref(), SStore::F64, c->x64.ref(), SStore::F64, c->r64.ref(), SStore::F64,
+                       c->p64.ref(), c->state, c->rs, c->stream);
+  }
+  LQ_CUDA(c, cudaGetLastError());
+  LQ_TRY(read_state(c));
+
+  lq_solve_stats& s = *sout;
+  s = lq_solve_stats{};
+  s.kernel_launches = mixed ? 2 : 1;      // (zero x,) initialise
+  lq_status result = LQ_OK;
+  double rel = 1.0;
+  if (c->state_host->breakdown) {
+    result = fail(c, LQ_ERR_NAN, "non-finite right-hand side");
+  } else if (c->state_host->phi2 == 0.0) {
+    rel = 0.0;
+    s.converged = 1;
+  } else {
+    const int chunk = mixed ? (reliable_every > 0 ? reliable_every : 32) : 16;
+    double best_rr = c->state_host->phi2;
+    int stagnant = 0;
+    for (long guard = 0; guard < (long)maxiter + 64; ++guard) {
+      LQ_TRY(run_chunk(c, inner, chunk, kappa));
+      s.kernel_launches += 3 * chunk;
+      LQ_TRY(read_state(c));
+      const SolverState& st = *c->state_host;
+      if (st.breakdown) { result = fail(c, LQ_ERR_NAN, "CG breakdown (non-positive or non-finite curvature)"); break; }
+      if (!st.halt) continue;
+      // true residual in FP64; for mixed solves this is the reliable update
+      if (mixed) launch_accumulate_x(g, slo, c->x_lo[k].ref(), c->x64.ref(), c->stream);
+      cg64_true_residual(c, kappa, inner, c->stream);
+      s.kernel_launches += mixed ? 3 : 2;
+      LQ_CUDA(c, cudaGetLastError());
+      LQ_TRY(read_state(c));
+      const double rr_true = c->state_host->rr_true;
+      rel = std::sqrt(rr_true / c->state_host->phi2);
+      if (mixed) s.reliable_updates++;
+      if (!std::isfinite(rel)) { result = fail(c, LQ_ERR_NAN, "non-finite residual"); break; }
+      if (rel <= tol) { s.converged = 1; break; }
+      if (c->state_host->iter >= maxiter) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "not converged after %d iterations (relative residual %.3e)",
+                      c->state_host->iter, rel);
+        result = fail(c, LQ_ERR_NOT_CONVERGED, buf);
+        break;
+      }
+      // FP64 CG: the recursion met tol but the true residual did not ->
+      // restart from the true residual.  Mixed: keep the search direction
+      // unless the true residual has stopped improving.
+      int restart = mixed ? 0 : 1;
+      if (mixed) {
+        if (rr_true < 0.5 * best_rr) { best_rr = rr_true; stagnant = 0; }
+        else if (++stagnant >= 3) { restart = 1; stagnant = 0; }
+      }
+      if (restart) s.restarts++;
+      launch_state_after_residual(c->state, restart, c->stream);
+      if (mixed) launch_xpay_p(g, slo, c->r_lo[k].ref(), c->p_lo[k].ref(), c->state, true, c->stream);
+      else launch_xpay_p(g, SStore::F64, c->r64.ref(), c->p64.ref(), c->state, true, c->stream);
+      s.kernel_launches += 2;
+      LQ_CUDA(c, cudaGetLastError());
+    }
+  }
+  s.iterations = c->state_host->iter;
+  s.true_rel_resid = rel;
+  return result;
+}
+
+lq_status ensure_md_fields(lq_ctx* c) {
+  const size_t mb = sizeof(double) * 32 * (size_t)c->geo.V;
+  if (!c->mom) LQ_CUDA(c, cudaMalloc(&c->mom, mb));
+  if (!c->mom0) LQ_CUDA(c, cudaMalloc(&c->mom0, mb));
+  if (!c->force) LQ_CUDA(c, cudaMalloc(&c->force, mb));
+  if (!c->gauge_old) LQ_CUDA(c, cudaMalloc(&c->gauge_old, gauge_bytes(GStore::F64_18, c->geo.V)));
+  LQ_TRY(alloc_field(c, c->y64, SStore::F64));
+  LQ_TRY(alloc_field(c, c->chi64, SStore::F64));
+  LQ_TRY(alloc_field(c, c->x64, SStore::F64));
+  LQ_TRY(alloc_field(c, c->phi64, SStore::F64));
+  return LQ_OK;
+}
+
+// canonical momenta / forces [V][32] (host or device) -> SoA [32][V]
+lq_status stage_mom_in(lq_ctx* c, const double* p, double* soa) {
+  if (!p) return fail(c, LQ_ERR_ARG, "null momentum buffer");
+  if (!aligned16(p)) return fail(c, LQ_ERR_ARG, "momentum buffer not 16-byte aligned");
+  const double* src = p;
+  if (!is_device_ptr(p)) {
+    if (!c->stage_mom) LQ_CUDA(c, cudaMalloc(&c->stage_mom, sizeof(double) * 32 * (size_t)c->geo.V));
+    LQ_CUDA(c, cudaMemcpyAsync(c->stage_mom, p, sizeof(double) * 32 * (size_t)c->geo.V, cudaMemcpyHostToDevice,
+                               c->stream));
+    src = c->stage_mom;
+  }
+  launch_pack_mom(c->geo, src, soa, c->stream);
+  LQ_CUDA(c, cudaGetLastError());
+  return LQ_OK;
+}
+
+lq_status deliver_mom(lq_ctx* c, const double* soa, double* out) {
+  if (!out) return fail(c, LQ_ERR_ARG, "null output buffer");
+  if (!aligned16(out)) return fail(c, LQ_ERR_ARG, "output buffer not 16-byte aligned");
+  if (is_device_ptr(out)) {
+    launch_unpack_mom(c->geo, soa, out, c->stream);
+    LQ_CUDA(c, cudaGetLastError());
+    return LQ_OK;
+  }
+  if (!c->stage_mom) LQ_CUDA(c, cudaMalloc(&c->stage_mom, sizeof(double) * 32 * (size_t)c->geo.V));
+  launch_unpack_mom(c->geo, soa, c->stage_mom, c->stream);
+  LQ_CUDA(c, cudaMemcpyAsync(out, c->stage_mom, sizeof(double) * 32 * (size_t)c->geo.V, cudaMemcpyDeviceToHost,
+                             c->stream));
+  LQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LQ_OK;
+}
+
+void gauge_changed(lq_ctx* c) {
+  for (int p = 0; p < kNumPrec; ++p) c->gauge_lo_valid[p] = false;
+}
+
+// p -= eps (F_gauge + F_fermion) at the current links; one solve for X = (M^dag M)^{-1} phi
+lq_status md_force_step(lq_ctx* c, const lq_hmc_params* hp, double eps, lq_traj_result* res) {
+  launch_gauge_force(c->geo, c->gauge64, c->mom, hp->beta, eps, true, c->stream);
+  lq_solve_stats s{};
+  lq_status st = solve_internal(c, hp->kappa, hp->tol, hp->maxiter, hp->inner_prec, hp->reliable_every, nullptr,
+                                0, &s);
+  res->solves += 1;
+  res->cg_iterations += s.iterations;
+  res->kernel_launches += s.kernel_launches + 3;
+  if (st != LQ_OK) return st;
+  apply_M_prec(c->geo, LQ_F64, c->gauge64, c->x64.ref(), c->y64.ref(), hp->kappa, false, c->stream);
+  launch_fermion_force(c->geo, c->gauge64, c->x64.ref(), c->y64.ref(), c->mom, hp->kappa, eps, true, c->stream);
+  LQ_CUDA(c, cudaGetLastError());
+  return LQ_OK;
+}
+
+lq_status read_scalars(lq_ctx* c) {
+  LQ_CUDA(c, cudaMemcpyAsync(c->dscalar_host, c->dscalar, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
+  LQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LQ_OK;
+}
+
 }  // namespace
 
 // Error text of calls that run without a context (read with lq_last_error(NULL)).
@@ -219,7 +380,10 @@ lq_status lq_destroy(lq_ctx* c) {
   if (c->stage_in) cudaFree(c->stage_in);
   if (c->stage_out) cudaFree(c->stage_out);
   if (c->stage_gauge) cudaFree(c->stage_gauge);
-  for (Field* f : {&c->phi64, &c->x64, &c->r64, &c->p64, &c->t64, &c->tmp64}) free_field(*f);
+  for (Field* f : {&c->phi64, &c->x64, &c->r64, &c->p64, &c->t64, &c->tmp64, &c->y64, &c->chi64}) free_field(*f);
+  for (double* d : {c->mom, c->mom0, c->force, c->stage_mom})
+    if (d) cudaFree(d);
+  if (c->gauge_old) cudaFree(c->gauge_old);
   for (int k = 0; k < 4; ++k) {
     free_field(c->r_lo[k]);
     free_field(c->p_lo[k]);
@@ -333,96 +497,15 @@ lq_status lq_solve_MdagM(lq_ctx* c, double* x, const double* phi, double kappa, 
   if (!(tol > 0.0) || maxiter <= 0 || reliable_every < 0 || (hist && hist_len < 0))
     return fail(c, LQ_ERR_ARG, "bad tolerance, iteration limit or history length");
   LQ_TRY(require_gauge(c, LQ_F64));
-  LQ_TRY(require_gauge(c, inner));
   LQ_TRY(ensure_solver_fields(c, inner));
-  const Geom& g = c->geo;
-  const bool mixed = inner != LQ_F64;
-  const SStore slo = spinor_store_of(inner);
-  const int k = (int)slo;
-
   double* hist_dev = nullptr;
   if (hist && hist_len > 0) LQ_CUDA(c, cudaMallocAsync((void**)&hist_dev, sizeof(double) * hist_len, c->stream));
-
   const double* dphi = nullptr;
   LQ_TRY(stage_spinor_in(c, phi, &dphi));
-  launch_pack_spinor(g, dphi, SStore::F64, c->phi64.ref(), c->stream);
-
-  SolverState h{};
-  h.stop2 = tol * tol;
-  h.ru_every = mixed ? reliable_every : 0;
-  h.delta2 = mixed ? 1e-4 : 0.0;          // reliable update once |r| fell by 1e-2
-  h.maxiter = maxiter;
-  h.hist = hist_dev;
-  h.hist_len = hist_dev ? hist_len : 0;
-  *c->state_host = h;
-  LQ_CUDA(c, cudaMemcpyAsync(c->state, c->state_host, sizeof(SolverState), cudaMemcpyHostToDevice, c->stream));
-  if (mixed) {
-    launch_zero_spinor(g, SStore::F64, c->x64.ref(), c->stream);
-    launch_solver_init(g, c->phi64.ref(), slo, c->x_lo[k].ref(), slo, c->r_lo[k].ref(), slo, c->p_lo[k].ref(),
-                       c->state, c->rs, c->stream);
-  } else {
-    launch_solver_init(g, c->phi64.ref(), SStore::F64, c->x64.ref(), SStore::F64, c->r64.ref(), SStore::F64,
-                       c->p64.ref(), c->state, c->rs, c->stream);
-  }
-  LQ_CUDA(c, cudaGetLastError());
-  LQ_TRY(read_state(c));
-
+  launch_pack_spinor(c->geo, dphi, SStore::F64, c->phi64.ref(), c->stream);
   lq_solve_stats s{};
-  s.kernel_launches = mixed ? 3 : 2;      // pack phi, (zero x,) initialise
-  lq_status result = LQ_OK;
-  double rel = 1.0;
-  if (c->state_host->breakdown) {
-    result = fail(c, LQ_ERR_NAN, "non-finite right-hand side");
-  } else if (c->state_host->phi2 == 0.0) {
-    rel = 0.0;
-    s.converged = 1;
-  } else {
-    const int chunk = mixed ? (reliable_every > 0 ? reliable_every : 32) : 16;
-    double best_rr = c->state_host->phi2;
-    int stagnant = 0;
-    for (long guard = 0; guard < (long)maxiter + 64; ++guard) {
-      LQ_TRY(run_chunk(c, inner, chunk, kappa));
-      s.kernel_launches += 3 * chunk;
-      LQ_TRY(read_state(c));
-      const SolverState& st = *c->state_host;
-      if (st.breakdown) { result = fail(c, LQ_ERR_NAN, "CG breakdown (non-positive or non-finite curvature)"); break; }
-      if (!st.halt) continue;
-      // true residual in FP64; for mixed solves this is the reliable update
-      if (mixed) launch_accumulate_x(g, slo, c->x_lo[k].ref(), c->x64.ref(), c->stream);
-      cg64_true_residual(c, kappa, inner, c->stream);
-      s.kernel_launches += mixed ? 3 : 2;
-      LQ_CUDA(c, cudaGetLastError());
-      LQ_TRY(read_state(c));
-      const double rr_true = c->state_host->rr_true;
-      rel = std::sqrt(rr_true / c->state_host->phi2);
-      if (mixed) s.reliable_updates++;
-      if (!std::isfinite(rel)) { result = fail(c, LQ_ERR_NAN, "non-finite residual"); break; }
-      if (rel <= tol) { s.converged = 1; break; }
-      if (c->state_host->iter >= maxiter) {
-        char buf[160];
-        std::snprintf(buf, sizeof buf, "not converged after %d iterations (relative residual %.3e)",
-                      c->state_host->iter, rel);
-        result = fail(c, LQ_ERR_NOT_CONVERGED, buf);
-        break;
-      }
-      // FP64 CG: the recursion met tol but the true residual did not ->
-      // restart from the true residual.  Mixed: keep the search direction
-      // unless the true residual has stopped improving.
-      int restart = mixed ? 0 : 1;
-      if (mixed) {
-        if (rr_true < 0.5 * best_rr) { best_rr = rr_true; stagnant = 0; }
-        else if (++stagnant >= 3) { restart = 1; stagnant = 0; }
-      }
-      if (restart) s.restarts++;
-      launch_state_after_residual(c->state, restart, c->stream);
-      if (mixed) launch_xpay_p(g, slo, c->r_lo[k].ref(), c->p_lo[k].ref(), c->state, true, c->stream);
-      else launch_xpay_p(g, SStore::F64, c->r64.ref(), c->p64.ref(), c->state, true, c->stream);
-      s.kernel_launches += 2;
-      LQ_CUDA(c, cudaGetLastError());
-    }
-  }
-  s.iterations = c->state_host->iter;
-  s.true_rel_resid = rel;
+  lq_status result = solve_internal(c, kappa, tol, maxiter, inner, reliable_every, hist_dev, hist_len, &s);
+  s.kernel_launches += 1;
   if (result == LQ_OK || result == LQ_ERR_NOT_CONVERGED) {
     lq_status d = deliver_spinor(c, c->x64, x);
     s.kernel_launches += 1;
@@ -492,6 +575,145 @@ lq_status lq_time_dslash(lq_ctx* c, const double* in, double kappa, int dagger, 
   cudaStreamSynchronize(c->stream);
   *ms = total / n;
   return st;
+}
+
+lq_status lq_plaquette(lq_ctx* c, double* plaq) {
+  if (!c) return LQ_ERR_ARG;
+  if (!plaq) return fail(c, LQ_ERR_ARG, "null output");
+  LQ_TRY(require_gauge(c, LQ_F64));
+  launch_plaquette(c->geo, c->gauge64, nullptr, c->rs, c->dscalar, c->stream);
+  LQ_CUDA(c, cudaGetLastError());
+  LQ_TRY(read_scalars(c));
+  *plaq = c->dscalar_host[0] / (18.0 * c->geo.V);
+  return LQ_OK;
+}
+
+lq_status lq_gauge_action(lq_ctx* c, double beta, double* S) {
+  if (!c) return LQ_ERR_ARG;
+  if (!S) return fail(c, LQ_ERR_ARG, "null output");
+  LQ_TRY(require_gauge(c, LQ_F64));
+  launch_plaquette(c->geo, c->gauge64, nullptr, c->rs, c->dscalar, c->stream);
+  LQ_CUDA(c, cudaGetLastError());
+  LQ_TRY(read_scalars(c));
+  *S = beta * (6.0 * c->geo.V - c->dscalar_host[0] / 3.0);
+  return LQ_OK;
+}
+
+lq_status lq_gauge_force(lq_ctx* c, double* F, double beta) {
+  if (!c) return LQ_ERR_ARG;
+  LQ_TRY(require_gauge(c, LQ_F64));
+  LQ_TRY(ensure_md_fields(c));
+  launch_gauge_force(c->geo, c->gauge64, c->force, beta, 0.0, false, c->stream);
+  LQ_CUDA(c, cudaGetLastError());
+  return deliver_mom(c, c->force, F);
+}
+
+lq_status lq_fermion_force(lq_ctx* c, double* F, const double* X, double kappa) {
+  if (!c) return LQ_ERR_ARG;
+  LQ_TRY(require_gauge(c, LQ_F64));
+  LQ_TRY(ensure_md_fields(c));
+  const double* dX = nullptr;
+  LQ_TRY(stage_spinor_in(c, X, &dX));
+  launch_pack_spinor(c->geo, dX, SStore::F64, c->x64.ref(), c->stream);
+  apply_M_prec(c->geo, LQ_F64, c->gauge64, c->x64.ref(), c->y64.ref(), kappa, false, c->stream);
+  launch_fermion_force(c->geo, c->gauge64, c->x64.ref(), c->y64.ref(), c->force, kappa, 0.0, false, c->stream);
+  LQ_CUDA(c, cudaGetLastError());
+  return deliver_mom(c, c->force, F);
+}
+
+lq_status lq_link_update(lq_ctx* c, const double* p, double eps) {
+  if (!c) return LQ_ERR_ARG;
+  LQ_TRY(require_gauge(c, LQ_F64));
+  LQ_TRY(ensure_md_fields(c));
+  LQ_TRY(stage_mom_in(c, p, c->mom));
+  launch_link_update(c->geo, c->gauge64, c->mom, eps, c->stream);
+  LQ_CUDA(c, cudaGetLastError());
+  gauge_changed(c);
+  if (!is_device_ptr(p)) LQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LQ_OK;
+}
+
+lq_status lq_hmc_trajectory(lq_ctx* c, const lq_hmc_params* hp, double* p, const double* chi, double u,
+                            lq_traj_result* out) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!c) return LQ_ERR_ARG;
+  if (!hp || !out) return fail(c, LQ_ERR_ARG, "null parameters or result");
+  if (hp->n_steps <= 0 || !(hp->tau > 0.0) || !(hp->tol > 0.0) || hp->maxiter <= 0 || hp->reliable_every < 0)
+    return fail(c, LQ_ERR_ARG, "bad trajectory parameters");
+  LQ_TRY(check_prec(c, hp->inner_prec));
+  LQ_TRY(require_gauge(c, LQ_F64));
+  LQ_TRY(ensure_md_fields(c));
+  LQ_TRY(ensure_solver_fields(c, hp->inner_prec));
+  lq_traj_result r{};
+  const Geom& g = c->geo;
+  // heat bath inputs: p (momenta) and chi; phi = M^dag chi
+  LQ_TRY(stage_mom_in(c, p, c->mom));
+  LQ_CUDA(c, cudaMemcpyAsync(c->mom0, c->mom, sizeof(double) * 32 * (size_t)g.V, cudaMemcpyDeviceToDevice,
+                             c->stream));
+  const double* dchi = nullptr;
+  LQ_TRY(stage_spinor_in(c, chi, &dchi));
+  launch_pack_spinor(g, dchi, SStore::F64, c->chi64.ref(), c->stream);
+  apply_M_prec(g, LQ_F64, c->gauge64, c->chi64.ref(), c->phi64.ref(), hp->kappa, true, c->stream);
+  LQ_CUDA(c, cudaMemcpyAsync(c->gauge_old, c->gauge64, gauge_bytes(GStore::F64_18, g.V), cudaMemcpyDeviceToDevice,
+                             c->stream));
+  r.kernel_launches += 4;
+  // leapfrog: half step in p, then n x (full step in U, full step in p), last p step halved
+  const double eps = hp->tau / hp->n_steps;
+  lq_status st = md_force_step(c, hp, 0.5 * eps, &r);
+  for (int i = 0; i < hp->n_steps && st == LQ_OK; ++i) {
+    launch_link_update(g, c->gauge64, c->mom, eps, c->stream);
+    gauge_changed(c);
+    r.kernel_launches += 1;
+    st = md_force_step(c, hp, i < hp->n_steps - 1 ? eps : 0.5 * eps, &r);
+  }
+  if (st == LQ_OK) {
+    // S_f at the end: X = (M^dag M)^{-1} phi on the new links
+    lq_solve_stats s{};
+    st = solve_internal(c, hp->kappa, hp->tol, hp->maxiter, hp->inner_prec, hp->reliable_every, nullptr, 0, &s);
+    r.solves += 1;
+    r.cg_iterations += s.iterations;
+    r.kernel_launches += s.kernel_launches;
+  }
+  if (st != LQ_OK) {
+    // leave the links as they were before the trajectory
+    cudaMemcpyAsync(c->gauge64, c->gauge_old, gauge_bytes(GStore::F64_18, g.V), cudaMemcpyDeviceToDevice, c->stream);
+    gauge_changed(c);
+    cudaStreamSynchronize(c->stream);
+    return st;
+  }
+  // Delta H from per-site differences
+  launch_fermion_action_diff(g, c->phi64.ref(), c->x64.ref(), c->chi64.ref(), c->rs, c->dscalar + 0, c->stream);
+  launch_kinetic_diff(g, c->mom, c->mom0, c->rs, c->dscalar + 1, c->stream);
+  launch_plaquette(g, c->gauge_old, c->gauge64, c->rs, c->dscalar + 2, c->stream);
+  r.kernel_launches += 3;
+  LQ_CUDA(c, cudaGetLastError());
+  LQ_TRY(read_scalars(c));
+  r.dSf = c->dscalar_host[0];
+  r.dK = c->dscalar_host[1];
+  r.dSg = hp->beta / 3.0 * c->dscalar_host[3];       // sum (ReTr P_old - ReTr P_new)
+  r.dH = r.dK + r.dSg + r.dSf;
+  if (!std::isfinite(r.dH)) {
+    cudaMemcpyAsync(c->gauge64, c->gauge_old, gauge_bytes(GStore::F64_18, g.V), cudaMemcpyDeviceToDevice, c->stream);
+    gauge_changed(c);
+    cudaStreamSynchronize(c->stream);
+    *out = r;
+    return fail(c, LQ_ERR_NAN, "non-finite Delta H; trajectory rejected");
+  }
+  r.accepted = (r.dH <= 0.0 || u < std::exp(-r.dH)) ? 1 : 0;
+  if (!r.accepted) {
+    LQ_CUDA(c, cudaMemcpyAsync(c->gauge64, c->gauge_old, gauge_bytes(GStore::F64_18, g.V),
+                               cudaMemcpyDeviceToDevice, c->stream));
+    gauge_changed(c);
+  }
+  launch_plaquette(g, c->gauge64, nullptr, c->rs, c->dscalar + 4, c->stream);
+  r.kernel_launches += 1;
+  LQ_TRY(read_scalars(c));
+  r.plaquette = c->dscalar_host[4] / (18.0 * g.V);
+  LQ_TRY(deliver_mom(c, c->mom, p));
+  LQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *out = r;
+  return LQ_OK;
 }
 
 }  // extern "C"

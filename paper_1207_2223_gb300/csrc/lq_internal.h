@@ -72,6 +72,16 @@ struct lq_ctx {
   // low-precision solver fields, one set per storage format
   lq::Field r_lo[4], p_lo[4], t_lo[4], x_lo[4];
 
+  // molecular dynamics: momenta / forces double [32][V], the start momenta,
+  // the force buffer, the gauge field at the start of a trajectory, Y = M X
+  // and the pseudofermion noise chi
+  double* mom = nullptr;
+  double* mom0 = nullptr;
+  double* force = nullptr;
+  double* stage_mom = nullptr;           // V * 32 doubles (canonical staging)
+  void* gauge_old = nullptr;
+  lq::Field y64, chi64;
+
   // reductions and solver scalars
   lq::ReduceScratch rs{};
   lq::SolverState* state = nullptr;      // device
@@ -115,4 +125,22 @@ void cg64_true_residual(lq_ctx* c, double kappa, int store_lo_prec, cudaStream_t
 // ---- low-precision CG iteration (k_cglo.cu)
 void cglo_iteration(lq_ctx* c, int prec, double kappa, cudaStream_t stream);
 
+}  // namespace lq
+
+namespace lq {
+// ---- gauge side (k_gauge.cu); momenta / forces are double [32][V]
+void launch_plaquette(const Geom& g, const void* ga, const void* gb, const ReduceScratch& rs, double* out,
+                      cudaStream_t st);
+void launch_gauge_force(const Geom& g, const void* gauge, double* f, double beta, double eps, bool update,
+                        cudaStream_t st);
+void launch_link_update(const Geom& g, void* gauge, const double* p, double eps, cudaStream_t st);
+void launch_pack_mom(const Geom& g, const double* canon, double* soa, cudaStream_t st);
+void launch_unpack_mom(const Geom& g, const double* soa, double* canon, cudaStream_t st);
+void launch_kinetic_diff(const Geom& g, const double* p, const double* p0, const ReduceScratch& rs, double* out,
+                         cudaStream_t st);
+// ---- fermion side (k_force.cu)
+void launch_fermion_force(const Geom& g, const void* gauge, SpinorRef X, SpinorRef Y, double* f, double kappa,
+                          double eps, bool update, cudaStream_t st);
+void launch_fermion_action_diff(const Geom& g, SpinorRef phi, SpinorRef X, SpinorRef chi, const ReduceScratch& rs,
+                                double* out, cudaStream_t st);
 }  // namespace lq

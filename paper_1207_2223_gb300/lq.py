@@ -33,6 +33,22 @@ class lq_solve_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class lq_hmc_params(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("kappa", ctypes.c_double), ("tau", ctypes.c_double),
+                ("n_steps", ctypes.c_int), ("tol", ctypes.c_double), ("maxiter", ctypes.c_int),
+                ("inner_prec", ctypes.c_int), ("reliable_every", ctypes.c_int)]
+
+
+class lq_traj_result(ctypes.Structure):
+    _fields_ = [("dH", ctypes.c_double), ("dK", ctypes.c_double), ("dSg", ctypes.c_double),
+                ("dSf", ctypes.c_double), ("accepted", ctypes.c_int), ("plaquette", ctypes.c_double),
+                ("solves", ctypes.c_int), ("cg_iterations", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _P = ctypes.c_void_p
 _D = ctypes.c_double
 _I = ctypes.c_int
@@ -52,6 +68,12 @@ SIGNATURES = {
     "lq_solve_MdagM": (_I, [_P, _P, _P, _D, _D, _I, _I, _I, _P, _I, ctypes.POINTER(lq_solve_stats)]),
     "lq_time_dslash": (_I, [_P, _P, _D, _I, _I, _I, _I, ctypes.POINTER(_D)]),
     "lq_apply_MdagM_static": (_I, [_P, _P, _P, ctypes.POINTER(_I), _I, _D, _P]),
+    "lq_plaquette": (_I, [_P, ctypes.POINTER(_D)]),
+    "lq_gauge_action": (_I, [_P, _D, ctypes.POINTER(_D)]),
+    "lq_gauge_force": (_I, [_P, _P, _D]),
+    "lq_fermion_force": (_I, [_P, _P, _P, _D]),
+    "lq_link_update": (_I, [_P, _P, _D]),
+    "lq_hmc_trajectory": (_I, [_P, ctypes.POINTER(lq_hmc_params), _P, _P, _D, ctypes.POINTER(lq_traj_result)]),
 }
 
 _lib = None
@@ -165,6 +187,40 @@ def lq_time_dslash(ctx, inp, kappa, dagger=False, prec=LQ_F64, n=20, flush_l2=Fa
     _check(ctx, load().lq_time_dslash(ctx, _ptr(inp), float(kappa), 1 if dagger else 0, int(prec), int(n),
                                       1 if flush_l2 else 0, ctypes.byref(ms)))
     return ms.value
+
+
+def lq_plaquette(ctx):
+    v = _D()
+    _check(ctx, load().lq_plaquette(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def lq_gauge_action(ctx, beta):
+    v = _D()
+    _check(ctx, load().lq_gauge_action(ctx, float(beta), ctypes.byref(v)))
+    return v.value
+
+
+def lq_gauge_force(ctx, F, beta):
+    _check(ctx, load().lq_gauge_force(ctx, _ptr(F), float(beta)))
+
+
+def lq_fermion_force(ctx, F, X, kappa):
+    _check(ctx, load().lq_fermion_force(ctx, _ptr(F), _ptr(X), float(kappa)))
+
+
+def lq_link_update(ctx, p, eps):
+    _check(ctx, load().lq_link_update(ctx, _ptr(p), float(eps)))
+
+
+def lq_hmc_trajectory(ctx, p, chi, u, beta, kappa, n_steps, tau=1.0, tol=1e-10, maxiter=100000,
+                      inner_prec=LQ_F64, reliable_every=50):
+    """One trajectory; p is updated in place.  Returns the result as a dict."""
+    hp = lq_hmc_params(float(beta), float(kappa), float(tau), int(n_steps), float(tol), int(maxiter),
+                       int(inner_prec), int(reliable_every))
+    res = lq_traj_result()
+    _check(ctx, load().lq_hmc_trajectory(ctx, ctypes.byref(hp), _ptr(p), _ptr(chi), float(u), ctypes.byref(res)))
+    return res.as_dict()
 
 
 def lq_apply_MdagM_static(out, U, inp, dims, kappa, t_antiperiodic=True, stream=None):

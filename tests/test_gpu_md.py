@@ -1,0 +1,164 @@
+"""Parity of the molecular-dynamics kernels (Sec. 3 kernels 2-4; Eq. 5) and of a
+whole HMC trajectory with the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle.fermion import fermion_force_from_X
+from oracle.gauge import gauge_action, gauge_force, plaquette
+from oracle.hmc import trajectory
+from oracle.su3 import link_update
+from synth import Lattice, gauge_exp_iA, source, momenta, chi_noise, metropolis_uniform, identity_gauge
+from tests.gpu_common import require_gpu, dev, host, rel_err, torch
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(4, 4, 4, 4), (2, 2, 2, 2), (6, 4, 2, 6), (3, 5, 2, 7)]
+
+
+@pytest.fixture(scope="module")
+def lq():
+    return require_gpu()
+
+
+def _ctx(lq, dims, U, t_antiperiodic=True):
+    ctx = lq.lq_create(dims, t_antiperiodic)
+    lq.lq_gauge_set(ctx, dev(U))
+    return ctx
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+def test_plaquette_and_action(lq, dims):
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, 0.4, 3)
+    ctx = _ctx(lq, dims, U)
+    try:
+        plaq = lq.lq_plaquette(ctx)
+        S = lq.lq_gauge_action(ctx, 5.6)
+        lq.lq_gauge_set(ctx, dev(identity_gauge(lat)))
+        one = lq.lq_plaquette(ctx)
+    finally:
+        lq.lq_destroy(ctx)
+    assert plaq == pytest.approx(plaquette(U, dims), rel=1e-13)
+    assert S == pytest.approx(gauge_action(U, dims, 5.6), rel=1e-12)
+    assert one == pytest.approx(1.0, abs=1e-15)
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+def test_gauge_force(lq, dims):
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, 0.4, 4)
+    ctx = _ctx(lq, dims, U)
+    try:
+        F = torch.empty((lat.V, 4, 8), dtype=torch.float64, device="cuda")
+        lq.lq_gauge_force(ctx, F, 5.6)
+        got = host(F)
+    finally:
+        lq.lq_destroy(ctx)
+    ref = gauge_force(U, dims, 5.6)
+    assert rel_err(got, ref) < 1e-12
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+@pytest.mark.parametrize("antiperiodic", [True, False])
+def test_fermion_force(lq, dims, antiperiodic):
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, 0.35, 5)
+    X = source(lat, 6)
+    ctx = _ctx(lq, dims, U, antiperiodic)
+    try:
+        F = np.empty((lat.V, 4, 8))                       # host buffer path
+        lq.lq_fermion_force(ctx, F, dev(X), 0.15)
+    finally:
+        lq.lq_destroy(ctx)
+    ref = fermion_force_from_X(U, X, dims, 0.15, antiperiodic)
+    assert rel_err(F, ref) < 1e-12
+    assert np.max(np.abs(F - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("eps", [0.1, 1.3])
+def test_link_update(lq, eps):
+    dims = (4, 2, 4, 6)
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, 0.3, 7)
+    p = momenta(lat, 7)
+    ctx = _ctx(lq, dims, U)
+    try:
+        lq.lq_link_update(ctx, dev(p), eps)
+        got = np.empty_like(U)
+        lq.lq_gauge_get(ctx, got)
+    finally:
+        lq.lq_destroy(ctx)
+    ref = link_update(U, p, eps)
+    assert np.max(np.abs(got - ref)) < 1e-13
+    assert np.max(np.abs(np.linalg.det(got) - 1)) < 1e-14
+
+
+def test_trajectory_small_preset_fp64(lq):
+    """4^4, beta 5.6, kappa 0.15, 10 steps, tau 1, sigma 0.3, seed 0: Delta H, the decision,
+    the plaquette, the final momenta and links against the oracle."""
+    dims = (4, 4, 4, 4)
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, 0.3, 0)
+    p0 = momenta(lat, 0)
+    chi = chi_noise(lat, 0)
+    u = metropolis_uniform(0)
+    ref = trajectory(U, p0, chi, u, dims, 5.6, 0.15, 10, 1.0, 1e-10)
+    ctx = _ctx(lq, dims, U)
+    try:
+        p = dev(p0)
+        r = lq.lq_hmc_trajectory(ctx, p, dev(chi), u, 5.6, 0.15, 10, 1.0, 1e-10, 10000, lq.LQ_F64)
+        Ug = np.empty_like(U)
+        lq.lq_gauge_get(ctx, Ug)
+        pg = host(p)
+    finally:
+        lq.lq_destroy(ctx)
+    assert abs(r["dH"] - ref["dH"]) < 1e-8, (r["dH"], ref["dH"])
+    assert abs(r["dSf"] - ref["dSf"]) < 1e-8 and abs(r["dSg"] - ref["dSg"]) < 1e-8
+    assert bool(r["accepted"]) == ref["accept"]
+    assert r["plaquette"] == pytest.approx(ref["plaquette"], abs=1e-12)
+    assert r["solves"] == 12
+    assert np.max(np.abs(pg - ref["p"])) < 1e-8
+    assert np.max(np.abs(Ug - ref["U"])) < 1e-10
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_trajectory_mixed_precision_solves(lq, prec):
+    """Same trajectory with mixed-precision solves (FP64 true residual 1e-10 each)."""
+    dims = (4, 4, 4, 4)
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, 0.3, 0)
+    p0 = momenta(lat, 0)
+    chi = chi_noise(lat, 0)
+    u = metropolis_uniform(0)
+    ref = trajectory(U, p0, chi, u, dims, 5.6, 0.15, 10, 1.0, 1e-10)
+    ctx = _ctx(lq, dims, U)
+    try:
+        r = lq.lq_hmc_trajectory(ctx, dev(p0), dev(chi), u, 5.6, 0.15, 10, 1.0, 1e-10, 10000, prec, 50)
+    finally:
+        lq.lq_destroy(ctx)
+    assert abs(r["dH"] - ref["dH"]) < 1e-6, (r["dH"], ref["dH"])
+    assert bool(r["accepted"]) == ref["accept"]
+
+
+def test_trajectory_reject_restores_links(lq):
+    """From a nearly ordered start (sigma 0.05) with 8 steps over tau 0.6 the energy error is
+    positive (Delta H ~ 3.9); with u just below 1 the trajectory is rejected and the links are
+    restored bit for bit."""
+    dims = (2, 2, 2, 4)
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, 0.05, 1)
+    p0, chi = momenta(lat, 1), chi_noise(lat, 1)
+    ref = trajectory(U, p0, chi, 0.999999, dims, 5.6, 0.12, 8, 0.6, 1e-11)
+    assert ref["dH"] > 1.0 and not ref["accept"]
+    ctx = _ctx(lq, dims, U)
+    try:
+        r = lq.lq_hmc_trajectory(ctx, dev(p0), dev(chi), 0.999999, 5.6, 0.12, 8, 0.6, 1e-11, 10000, lq.LQ_F64)
+        Ug = np.empty_like(U)
+        lq.lq_gauge_get(ctx, Ug)
+    finally:
+        lq.lq_destroy(ctx)
+    assert r["accepted"] == 0
+    assert abs(r["dH"] - ref["dH"]) < 1e-9
+    assert np.array_equal(Ug, U)
+    assert r["plaquette"] == pytest.approx(plaquette(U, dims), abs=1e-13)
