@@ -38,18 +38,24 @@ DIMS = (32, 32, 32, 64)
 SIGMA, SEED, KAPPA, TOL, RELIABLE = 0.25, 2, 0.156, 1e-10, 50
 WORKLOAD = "cg_32x32x32x64"
 
-# Algorithmic (DRAM-minimal) bytes per site of one application of M: every
-# link and spinor moved once (gauge + input spinor + output spinor).
-DSLASH_BYTES = {"f64": 960, "f32": 480, "f32_12": 384, "f16_12": 200, "bf16_12": 200}
+# Algorithmic (DRAM-minimal) bytes per site, every link and spinor moved once.
+GAUGE_B = {"f64": 576, "f32": 288, "f32_12": 192, "f16_12": 96, "bf16_12": 96}
+SPINOR_B = {"f64": 192, "f32": 96, "f32_12": 96, "f16_12": 52, "bf16_12": 52}   # 16-bit: 48 + 4-byte norm
+# one application of M: gauge + input spinor + output spinor
+DSLASH_BYTES = {k: GAUGE_B[k] + 2 * SPINOR_B[k] for k in GAUGE_B}
+# the three passes of a CG iteration:
+#   k1  t = M p, |t|^2                          gauge + p + t
+#   k2  r -= alpha M^dag t, x += alpha p, |r|^2  gauge + t + r (read, write) + x (read, write) + p
+#   k3  p = r + beta p                          r + p (read, write)
+CG_BYTES = {k: {"k1": GAUGE_B[k] + 2 * SPINOR_B[k], "k2": GAUGE_B[k] + 6 * SPINOR_B[k], "k3": 3 * SPINOR_B[k]}
+            for k in GAUGE_B}
 DSLASH_FLOPS = 1368
 # DRAM traffic per site of the plain Dslash from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum over sites), valid for the kernel sources with this
 # hash; see profiles/.  Null when the kernel changed since the capture.
 NCU_TRAFFIC = {
-    # profiles/dslash_f32_12_32x32x32x32.md: 314.72 MB read + 82.42 MB written over 32^4 sites
-    "f32_12": {"bytes_per_site": 378.7, "src": "e3579385ca518247"},
-    # profiles/dslash_f16_12_32x32x32x32.md: 159.42 MB read + 37.24 MB written over 32^4 sites
-    "f16_12": {"bytes_per_site": 187.6, "src": "e3579385ca518247"},
+    # profiles/cg_pass2_f32_12_32x32x32x32.md: 617.80 MB read + 173.37 MB written over 32^4 sites
+    "f32_12": {"bytes_per_site": 754.5, "src": "6a8892349e2b3f82"},
 }
 
 
@@ -158,8 +164,8 @@ def run_reference(args):
     return 0
 
 
-def run_dslash_only(args):
-    """Profiling target: a few applications of M in one precision (no timing output)."""
+def run_kernel_only(args):
+    """Profiling target: a few launches of one kernel (--kernel-only dslash|k1|k2|k3) in one precision."""
     import torch
     import paper_1207_2223_gb300 as lq
     from synth import Lattice, gauge_exp_iA, source
@@ -168,10 +174,14 @@ def run_dslash_only(args):
     U, phi = gauge_exp_iA(lat, SIGMA, SEED), source(lat, SEED)
     ctx = lq.lq_create(dims)
     lq.lq_gauge_set(ctx, torch.from_numpy(U).cuda())
-    ms = lq.lq_time_dslash(ctx, torch.from_numpy(phi).cuda(), KAPPA, False, lq.PRECISIONS[args.dslash_only],
-                           args.steps, False)
+    p = torch.from_numpy(phi).cuda()
+    prec = lq.PRECISIONS[args.prec]
+    if args.kernel_only == "dslash":
+        ms = lq.lq_time_dslash(ctx, p, KAPPA, False, prec, args.steps, False)
+    else:
+        ms = lq.lq_time_cg_kernel(ctx, p, KAPPA, int(args.kernel_only[1]), prec, args.steps)
     lq.lq_destroy(ctx)
-    print("dslash %s %s: %.4f ms" % (args.dslash_only, dims, ms))
+    print("%s %s %s: %.4f ms" % (args.kernel_only, args.prec, dims, ms))
     return 0
 
 
@@ -230,7 +240,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         fp64_s = t0.elapsed_time(t1) / 1e3
 
-        # the dominant kernel, timed alone with CUDA events on the library's stream
+        # kernels timed alone with CUDA events on the library's stream
         peaks, peak_kind = load_peaks()
         hbm = float(peaks["hbm_gbs"])
         dsl = {}
@@ -239,14 +249,24 @@ def run_ours(args):
             gbs = DSLASH_BYTES[name] * V / (ms * 1e-3) / 1e9
             dsl[name] = {"ms": round(ms, 5), "GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4),
                          "GFLOP/s": round(DSLASH_FLOPS * V / (ms * 1e-3) / 1e9, 1)}
+        cg = {}
+        for which in ("k1", "k2", "k3"):
+            ms = lq.lq_time_cg_kernel(ctx, phid, KAPPA, int(which[1]), inner, 40)
+            gbs = CG_BYTES[args.inner][which] * V / (ms * 1e-3) / 1e9
+            cg[which] = {"ms": round(ms, 5), "GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4),
+                         "bytes_per_site": CG_BYTES[args.inner][which]}
+        cg["iteration_ms"] = round(lq.lq_time_cg_kernel(ctx, phid, KAPPA, 0, inner, 40), 5)
         src_hash = kernel_source_hash()
         tr = NCU_TRAFFIC.get(args.inner)
         traffic = tr["bytes_per_site"] * V if tr and tr.get("src") == src_hash else None
-        d = dsl[args.inner]
-        roofline = {"kernel": "dslash_kernel<%s> (M, store epilogue)" % args.inner, "bound": "hbm",
+        d = cg["k2"]
+        # the dominant kernel of the timed step (largest share of the launch list):
+        # CG pass 2, r -= alpha M^dag t, x += alpha p, |r|^2
+        roofline = {"kernel": "dslash_kernel<%s, M^dag, EpiCG2> (CG pass 2)" % args.inner, "bound": "hbm",
                     "achieved": d["GB/s"], "peak": hbm, "unit": "GB/s", "frac": d["frac_hbm"],
                     "traffic": traffic, "peak_kind": peak_kind,
-                    "bytes_per_site": DSLASH_BYTES[args.inner], "sites_per_launch": V}
+                    "bytes_per_site": CG_BYTES[args.inner]["k2"], "sites_per_launch": V,
+                    "launch_ms": d["ms"]}
 
         # end to end through the C interface with pinned host buffers
         Uh = torch.from_numpy(U).pin_memory()
@@ -289,7 +309,7 @@ def run_ours(args):
             "iterations": {"mixed": stats[-1]["iterations"], "reliable_updates": stats[-1]["reliable_updates"],
                            "fp64": st64["iterations"]},
             "true_rel_resid": {"mixed": stats[-1]["true_rel_resid"], "fp64": st64["true_rel_resid"]},
-            "roofline": roofline, "dslash": dsl, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+            "roofline": roofline, "cg_kernels": cg, "dslash": dsl, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -308,13 +328,15 @@ def main():
     ap.add_argument("--ref-site-fraction", type=int, default=8)
     ap.add_argument("--cg-iterations", type=int, default=312,
                     help="FP64 CG iterations of this workload (reference arm extrapolation)")
-    ap.add_argument("--dslash-only", default=None, help="profiling target: only time M in this precision")
+    ap.add_argument("--kernel-only", default=None, choices=["dslash", "k1", "k2", "k3"],
+                    help="profiling target: only launch this kernel (precision --prec)")
+    ap.add_argument("--prec", default="f32_12", choices=["f64", "f32", "f32_12", "f16_12", "bf16_12"])
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.dslash_only:
-        return run_dslash_only(args)
+    if args.kernel_only:
+        return run_kernel_only(args)
     return run_ours(args)
 
 

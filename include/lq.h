@@ -81,6 +81,7 @@ typedef struct {
   double true_rel_resid;    /* ||phi - M^dag M x|| / ||phi||, recomputed in FP64 */
   double seconds;           /* host wall-clock of the call, from entry to the final synchronisation */
   int64_t kernel_launches;  /* kernels this call launched (every node of a CUDA graph counts once) */
+  int escalations;          /* times the inner precision was raised to FP32 because it stagnated */
 } lq_solve_stats;
 
 /* Library version string. */
@@ -133,7 +134,10 @@ lq_status lq_apply_MdagM(lq_ctx* ctx, double* out, const double* in, double kapp
  *                   `reliable_every` iterations (0 = only when the iterated
  *                   residual has dropped by 1e-2 since the last update, or
  *                   has met tol) the low-precision solution is added to
- *                   the FP64 one and the FP64 residual is recomputed.
+ *                   the FP64 one and the FP64 residual is recomputed.  If
+ *                   three reliable updates in a row fail to halve the true
+ *                   residual, the iterations continue in FP32 from there
+ *                   (counted in stats->escalations).
  *   maxiter         iteration limit (> 0)
  *   hist, hist_len  optional host array receiving the relative iterated
  *                   residual of each iteration (NULL / 0 to skip)
@@ -186,6 +190,20 @@ lq_status lq_gauge_force(lq_ctx* ctx, double* F, double beta);
  * the solution X = (M^dag M)^{-1} phi (canonical spinor); Y = M X is formed inside
  * (Sec. 3 kernel 3).  F: canonical [V][4][8].  FP64. */
 lq_status lq_fermion_force(lq_ctx* ctx, double* F, const double* X, double kappa);
+
+/* Complex gradient G = dS_f / dconj(U) of S_f = phi^dag (M^dag M)^{-1} phi with respect
+ * to the entries of the gauge field, given X = (M^dag M)^{-1} phi: the convention of
+ * torch.autograd for a real function of complex inputs (dS = Re sum conj(G) dU).  The
+ * su(3) force of lq_fermion_force is F_a = -Im tr(t_a U G^dag).  Adjoint of the fermion
+ * part of Eq. 5 (the derivative behind Sec. 3 kernel 3).  G: canonical [V][4][3][3]
+ * complex.  FP64. */
+lq_status lq_fermion_grad(lq_ctx* ctx, double* G, const double* X, double kappa);
+
+/* S_f = phi^dag (M^dag M)^{-1} phi (the pseudofermion term of Eq. 4, 5): one solve
+ * (arguments as in lq_solve_MdagM) and an FP64 reduction; *S on the host; X, when not
+ * NULL, receives the solution.  Synchronises. */
+lq_status lq_pseudofermion_action(lq_ctx* ctx, const double* phi, double kappa, double tol, int maxiter,
+                                  int inner_prec, int reliable_every, double* S, double* X);
 
 /* Link update U_mu(x) <- exp(i eps P_mu(x)) U_mu(x), P = sum_a p_a t_a, then
  * reunitarisation (Gram-Schmidt rows 1, 2; row 3 = conj(row1 x row2)) (Sec. 3
@@ -245,6 +263,14 @@ lq_status lq_time_dslash(lq_ctx* ctx, const double* in, double kappa, int dagger
  * lq_last_error(NULL). */
 lq_status lq_apply_MdagM_static(double* out, const double* U, const double* in, const int dims[4],
                                 int t_antiperiodic, double kappa, void* cuda_stream);
+
+/* Measurement: the average device time in *ms of one CG iteration (which = 0)
+ * or of one of its three passes (1: t = M p with |t|^2; 2: r -= alpha M^dag t,
+ * x += alpha p with |r|^2; 3: p = r + beta p) in precision `prec`, run `n`
+ * times on a CG state started from `in` (canonical spinor) that never halts.
+ * CUDA events on the context's stream; the context's solver fields are
+ * overwritten.  The iteration is the paper's CG routine (Sec. 3).  Synchronises. */
+lq_status lq_time_cg_kernel(lq_ctx* ctx, const double* in, double kappa, int which, int prec, int n, double* ms);
 
 #ifdef __cplusplus
 }

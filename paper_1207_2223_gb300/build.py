@@ -31,21 +31,26 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def build(verbose=False, extra=None, force=False):
-    """Build liblq.so (skipped when it is newer than every source)."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, extra=None, force=False, out=None):
+    """Build liblq.so (skipped when it is newer than every source).
+
+    ``extra`` adds nvcc flags; ``out`` writes the library (and its objects)
+    to another path, e.g. to compare compile-time variants."""
+    lib = out or LIB
+    objdir = os.path.join(os.path.dirname(lib), "obj_" + os.path.basename(lib).replace(".", "_")) if out else BUILD
+    os.makedirs(objdir, exist_ok=True)
     srcs = sources()
     deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     deps.append(os.path.join(os.path.dirname(HERE), "include", "lq.h"))
-    if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(d) for d in deps):
-        return LIB
+    if not force and os.path.exists(lib) and all(os.path.getmtime(lib) >= os.path.getmtime(d) for d in deps):
+        return lib
     flags = FLAGS + list(extra or [])
     if verbose:
         flags += ["-Xptxas", "-v"]
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc] + ARCH + flags + ["-c", src, "-o", obj]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
@@ -58,13 +63,13 @@ def build(verbose=False, extra=None, force=False):
         for obj, log in results:
             if log.strip():
                 print("==", os.path.basename(obj), "\n", log)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcudart"]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError("link failed:\n" + p.stdout + p.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -152,6 +152,16 @@ lq_status read_state(lq_ctx* c) {
   return LQ_OK;
 }
 
+// Reliable update when the iterated residual fell by this factor (squared)
+// since the last one: 16-bit storage loses accuracy faster than FP32.
+double reliable_delta2(int inner) {
+  switch (inner) {
+    case LQ_BF16_12: return 1e-2;
+    case LQ_F16_12: return 1e-4;
+    default: return 1e-4;
+  }
+}
+
 // Solve M^dag M x = phi with phi already in c->phi64; the solution is left in
 // c->x64.  Host scalars come back once per CUDA graph of iterations.
 lq_status solve_internal(lq_ctx* c, double kappa, double tol, int maxiter, int inner, int reliable_every,
@@ -160,12 +170,12 @@ lq_status solve_internal(lq_ctx* c, double kappa, double tol, int maxiter, int i
   LQ_TRY(ensure_solver_fields(c, inner));
   const Geom& g = c->geo;
   const bool mixed = inner != LQ_F64;
-  const SStore slo = spinor_store_of(inner);
-  const int k = (int)slo;
+  SStore slo = spinor_store_of(inner);
+  int k = (int)slo;
   SolverState h{};
   h.stop2 = tol * tol;
   h.ru_every = mixed ? reliable_every : 0;
-  h.delta2 = mixed ? 1e-4 : 0.0;          // reliable update once |r| fell by 1e-2
+  h.delta2 = mixed ? reliable_delta2(inner) : 0.0;
   h.maxiter = maxiter;
   h.hist = hist_dev;
   h.hist_len = hist_dev ? hist_len : 0;
@@ -228,6 +238,29 @@ lq_status solve_internal(lq_ctx* c, double kappa, double tol, int maxiter, int i
       if (mixed) {
         if (rr_true < 0.5 * best_rr) { best_rr = rr_true; stagnant = 0; }
         else if (++stagnant >= 3) { restart = 1; stagnant = 0; }
+      }
+      if (restart && mixed && inner != LQ_F32) {
+        // Defect correction fallback: the inner precision cannot make progress
+        // on this system (its rounding times the condition number is too
+        // large), so continue in FP32 from the FP64 iterate and residual.
+        inner = LQ_F32;
+        slo = SStore::F32;
+        k = (int)slo;
+        LQ_TRY(require_gauge(c, inner));
+        LQ_TRY(ensure_solver_fields(c, inner));
+        launch_inner_restart(g, c->r64.ref(), slo, c->x_lo[k].ref(), c->r_lo[k].ref(), c->p_lo[k].ref(), c->stream);
+        SolverState& hs = *c->state_host;
+        hs.rr = hs.rr_prev = hs.rr_ref = rr_true;
+        hs.beta = 0.0;
+        hs.iter_since_ru = 0;
+        hs.halt = 0;
+        hs.delta2 = reliable_delta2(inner);
+        LQ_CUDA(c, cudaMemcpyAsync(c->state, c->state_host, sizeof(SolverState), cudaMemcpyHostToDevice, c->stream));
+        s.restarts++;
+        s.escalations++;
+        s.kernel_launches += 1;
+        LQ_CUDA(c, cudaGetLastError());
+        continue;
       }
       if (restart) s.restarts++;
       launch_state_after_residual(c->state, restart, c->stream);
@@ -621,6 +654,52 @@ lq_status lq_fermion_force(lq_ctx* c, double* F, const double* X, double kappa) 
   return deliver_mom(c, c->force, F);
 }
 
+lq_status lq_fermion_grad(lq_ctx* c, double* G, const double* X, double kappa) {
+  if (!c) return LQ_ERR_ARG;
+  if (!G) return fail(c, LQ_ERR_ARG, "null gradient buffer");
+  if (!aligned16(G)) return fail(c, LQ_ERR_ARG, "gradient buffer not 16-byte aligned");
+  LQ_TRY(require_gauge(c, LQ_F64));
+  LQ_TRY(ensure_md_fields(c));
+  const double* dX = nullptr;
+  LQ_TRY(stage_spinor_in(c, X, &dX));
+  launch_pack_spinor(c->geo, dX, SStore::F64, c->x64.ref(), c->stream);
+  apply_M_prec(c->geo, LQ_F64, c->gauge64, c->x64.ref(), c->y64.ref(), kappa, false, c->stream);
+  const size_t bytes = sizeof(double) * 72 * (size_t)c->geo.V;
+  if (is_device_ptr(G)) {
+    launch_fermion_grad(c->geo, c->x64.ref(), c->y64.ref(), G, kappa, c->stream);
+    LQ_CUDA(c, cudaGetLastError());
+    return LQ_OK;
+  }
+  if (!c->stage_gauge) LQ_CUDA(c, cudaMalloc(&c->stage_gauge, bytes));
+  launch_fermion_grad(c->geo, c->x64.ref(), c->y64.ref(), c->stage_gauge, kappa, c->stream);
+  LQ_CUDA(c, cudaGetLastError());
+  LQ_CUDA(c, cudaMemcpyAsync(G, c->stage_gauge, bytes, cudaMemcpyDeviceToHost, c->stream));
+  LQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LQ_OK;
+}
+
+lq_status lq_pseudofermion_action(lq_ctx* c, const double* phi, double kappa, double tol, int maxiter, int inner,
+                                  int reliable_every, double* S, double* X) {
+  if (!c) return LQ_ERR_ARG;
+  if (!S) return fail(c, LQ_ERR_ARG, "null output");
+  LQ_TRY(check_prec(c, inner));
+  if (!(tol > 0.0) || maxiter <= 0 || reliable_every < 0)
+    return fail(c, LQ_ERR_ARG, "bad tolerance or iteration limit");
+  LQ_TRY(require_gauge(c, LQ_F64));
+  LQ_TRY(ensure_solver_fields(c, inner));
+  const double* dphi = nullptr;
+  LQ_TRY(stage_spinor_in(c, phi, &dphi));
+  launch_pack_spinor(c->geo, dphi, SStore::F64, c->phi64.ref(), c->stream);
+  lq_solve_stats s{};
+  LQ_TRY(solve_internal(c, kappa, tol, maxiter, inner, reliable_every, nullptr, 0, &s));
+  launch_dot_re(c->geo, c->phi64.ref(), c->x64.ref(), c->rs, c->dscalar, c->stream);
+  LQ_CUDA(c, cudaGetLastError());
+  if (X) LQ_TRY(deliver_spinor(c, c->x64, X));
+  LQ_TRY(read_scalars(c));
+  *S = c->dscalar_host[0];
+  return LQ_OK;
+}
+
 lq_status lq_link_update(lq_ctx* c, const double* p, double eps) {
   if (!c) return LQ_ERR_ARG;
   LQ_TRY(require_gauge(c, LQ_F64));
@@ -714,6 +793,58 @@ lq_status lq_hmc_trajectory(lq_ctx* c, const lq_hmc_params* hp, double* p, const
   r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = r;
   return LQ_OK;
+}
+
+lq_status lq_time_cg_kernel(lq_ctx* c, const double* in, double kappa, int which, int prec, int n, double* ms) {
+  if (!c) return LQ_ERR_ARG;
+  if (!ms || n <= 0 || which < 0 || which > 3) return fail(c, LQ_ERR_ARG, "need 0 <= which <= 3, n > 0, ms");
+  LQ_TRY(check_prec(c, prec));
+  LQ_TRY(require_gauge(c, LQ_F64));
+  LQ_TRY(require_gauge(c, prec));
+  LQ_TRY(ensure_solver_fields(c, prec));
+  const Geom& g = c->geo;
+  const bool lo = prec != LQ_F64;
+  const SStore s = spinor_store_of(prec);
+  const int k = (int)s;
+  Field& r = lo ? c->r_lo[k] : c->r64;
+  Field& p = lo ? c->p_lo[k] : c->p64;
+  Field& t = lo ? c->t_lo[k] : c->t64;
+  Field& x = lo ? c->x_lo[k] : c->x64;
+  const double* din = nullptr;
+  LQ_TRY(stage_spinor_in(c, in, &din));
+  launch_pack_spinor(g, din, SStore::F64, c->phi64.ref(), c->stream);
+  // a state that never halts: stop2 = 0, no reliable updates, no iteration limit
+  SolverState h{};
+  h.maxiter = 0x7fffffff;
+  *c->state_host = h;
+  LQ_CUDA(c, cudaMemcpyAsync(c->state, c->state_host, sizeof(SolverState), cudaMemcpyHostToDevice, c->stream));
+  launch_solver_init(g, c->phi64.ref(), s, x.ref(), s, r.ref(), s, p.ref(), c->state, c->rs, c->stream);
+  if (lo) cglo_iteration(c, prec, kappa, c->stream);
+  else cg64_iteration(c, kappa, c->stream);
+  LQ_CUDA(c, cudaGetLastError());
+  cudaEvent_t e0, e1;
+  LQ_CUDA(c, cudaEventCreate(&e0));
+  LQ_CUDA(c, cudaEventCreate(&e1));
+  cudaEventRecord(e0, c->stream);
+  for (int i = 0; i < n; ++i) {
+    if (which == 0) {
+      if (lo) cglo_iteration(c, prec, kappa, c->stream);
+      else cg64_iteration(c, kappa, c->stream);
+    } else if (which == 3) {
+      launch_xpay_p(g, s, r.ref(), p.ref(), c->state, true, c->stream);
+    } else {
+      cg_step(c, prec, which, kappa, c->stream);
+    }
+  }
+  cudaEventRecord(e1, c->stream);
+  lq_status st = cuda_check(c, cudaEventSynchronize(e1), "cudaEventSynchronize");
+  float tms = 0.f;
+  cudaEventElapsedTime(&tms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == LQ_OK) st = cuda_check(c, cudaGetLastError(), "cg kernel launch");
+  *ms = tms / n;
+  return st;
 }
 
 }  // extern "C"

@@ -76,6 +76,21 @@ __global__ void __launch_bounds__(kBS) zero_spinor_kernel(int V, SpinorRef f) {
   store_spinor<S, double>(f, V, s, z);
 }
 
+// Restart the inner iteration from an FP64 residual: r = p = src, x = 0.
+template <SStore S>
+__global__ void __launch_bounds__(kBS) inner_restart_kernel(int V, SpinorRef src64, SpinorRef x, SpinorRef r,
+                                                            SpinorRef p) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  cplx<double> v[12], z[12];
+  load_spinor<SStore::F64, double>(src64, V, s, v);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) z[k] = {0.0, 0.0};
+  store_spinor<S, double>(x, V, s, z);
+  store_spinor<S, double>(r, V, s, v);
+  store_spinor<S, double>(p, V, s, v);
+}
+
 __global__ void state_after_residual_kernel(SolverState* st, int restart) {
   const double rr = st->rr_true;
   st->beta = restart ? 0.0 : rr / st->rr_prev;
@@ -115,6 +130,12 @@ void launch_accumulate_x(const Geom& g, SStore slo, SpinorRef xlo, SpinorRef xhi
 void launch_zero_spinor(const Geom& g, SStore s, SpinorRef f, cudaStream_t stream) {
   const int grid = grid_for(g.V, kBS);
   LQ_DISPATCH_S(s, (zero_spinor_kernel<SS><<<grid, kBS, 0, stream>>>(g.V, f)));
+}
+
+void launch_inner_restart(const Geom& g, SpinorRef src64, SStore s, SpinorRef x, SpinorRef r, SpinorRef p,
+                          cudaStream_t stream) {
+  const int grid = grid_for(g.V, kBS);
+  LQ_DISPATCH_S(s, (inner_restart_kernel<SS><<<grid, kBS, 0, stream>>>(g.V, src64, x, r, p)));
 }
 
 void launch_state_after_residual(SolverState* st, int restart, cudaStream_t stream) {

@@ -9,6 +9,18 @@
 
 namespace lq {
 
+void cg64_step(lq_ctx* c, int which, double kappa, cudaStream_t stream) {
+  const Geom& g = c->geo;
+  GaugeRef U{c->gauge64};
+  if (which == 1) {
+    EpiCG1<SStore::F64> e1{c->t64.ref(), c->state};
+    launch_dslash<double, GStore::F64_18, SStore::F64, false>(g, U, c->p64.ref(), kappa, e1, c->rs, stream);
+  } else {
+    EpiCG2<SStore::F64, SStore::F64, SStore::F64> e2{c->r64.ref(), c->x64.ref(), c->p64.ref(), c->state};
+    launch_dslash<double, GStore::F64_18, SStore::F64, true>(g, U, c->t64.ref(), kappa, e2, c->rs, stream);
+  }
+}
+
 void cg64_iteration(lq_ctx* c, double kappa, cudaStream_t stream) {
   const Geom& g = c->geo;
   GaugeRef U{c->gauge64};

@@ -18,6 +18,31 @@ static void iteration(lq_ctx* c, const void* gauge, double kappa, cudaStream_t s
   launch_xpay_p(g, S, c->r_lo[k].ref(), c->p_lo[k].ref(), c->state, false, stream);
 }
 
+template <GStore G, SStore S>
+static void step(lq_ctx* c, const void* gauge, int which, double kappa, cudaStream_t stream) {
+  const Geom& g = c->geo;
+  GaugeRef U{gauge};
+  const int k = (int)S;
+  if (which == 1) {
+    EpiCG1<S> e1{c->t_lo[k].ref(), c->state};
+    launch_dslash<float, G, S, false>(g, U, c->p_lo[k].ref(), kappa, e1, c->rs, stream);
+  } else {
+    EpiCG2<S, S, S> e2{c->r_lo[k].ref(), c->x_lo[k].ref(), c->p_lo[k].ref(), c->state};
+    launch_dslash<float, G, S, true>(g, U, c->t_lo[k].ref(), kappa, e2, c->rs, stream);
+  }
+}
+
+void cglo_step(lq_ctx* c, int prec, int which, double kappa, cudaStream_t stream) {
+  const void* gauge = c->gauge_lo[prec];
+  switch (prec) {
+    case LQ_F32: step<GStore::F32_18, SStore::F32>(c, gauge, which, kappa, stream); break;
+    case LQ_F32_12: step<GStore::F32_12, SStore::F32>(c, gauge, which, kappa, stream); break;
+    case LQ_F16_12: step<GStore::F16_12, SStore::F16>(c, gauge, which, kappa, stream); break;
+    case LQ_BF16_12: step<GStore::BF16_12, SStore::BF16>(c, gauge, which, kappa, stream); break;
+    default: break;
+  }
+}
+
 void cglo_iteration(lq_ctx* c, int prec, double kappa, cudaStream_t stream) {
   const void* gauge = c->gauge_lo[prec];
   switch (prec) {

@@ -106,6 +106,88 @@ __global__ void __launch_bounds__(kBS) fermion_action_diff_kernel(int V, SpinorR
   if (grid_sum<1>(red, rs, tot)) out[0] = tot[0];
 }
 
+// Complex gradient of S_f with respect to the entries of U_mu(x) in the
+// convention dS = Re sum conj(G) dU (that of torch.autograd):
+//   G = conj(2 kappa s C),  C_ij = sum_spin conj(((1 - g_mu) Y(x))_i) X(x+mu)_j
+//                                + sum_spin conj(X(x)_i) ((1 + g_mu) Y(x+mu))_j,
+// each spin sum again over the two half-spinor components.  G is written in
+// the canonical layout [V][4][3][3] complex.
+template <int MU>
+__device__ __forceinline__ M3 grad_matrix(const cplx<double> Xx[12], const cplx<double> Yx[12],
+                                          const cplx<double> Xf[12], const cplx<double> Yf[12]) {
+  cplx<double> a0[3], a1[3], b0[3], b1[3];
+  M3 C;
+  project<MU, -1>(Yx, a0, a1);
+  project<MU, -1>(Xf, b0, b1);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cplx<double> t = cjmul(a0[i], b0[j]);
+      C.m[3 * i + j] = cjmadd(t, a1[i], b1[j]);
+    }
+  project<MU, +1>(Xx, a0, a1);
+  project<MU, +1>(Yf, b0, b1);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cplx<double> t = cjmadd(C.m[3 * i + j], a0[i], b0[j]);
+      C.m[3 * i + j] = cjmadd(t, a1[i], b1[j]);
+    }
+  return C;
+}
+
+__global__ void __launch_bounds__(kBS) fermion_grad_kernel(Geom geo, SpinorRef X, SpinorRef Y, double2* G,
+                                                           double kappa) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 4 * geo.V) return;
+  const int mu = idx / geo.V, s = idx - mu * geo.V;
+  int c[4];
+  site_coords(geo, s, c);
+  const int xf = nbr_fwd(geo, s, c, mu);
+  const double sign = (mu == 3 && geo.antiperiodic && c[3] == geo.L[3] - 1) ? -1.0 : 1.0;
+  cplx<double> Xx[12], Yx[12], Xf[12], Yf[12];
+  load_spinor<SStore::F64, double>(X, geo.V, s, Xx);
+  load_spinor<SStore::F64, double>(Y, geo.V, s, Yx);
+  load_spinor<SStore::F64, double>(X, geo.V, xf, Xf);
+  load_spinor<SStore::F64, double>(Y, geo.V, xf, Yf);
+  M3 C;
+  switch (mu) {
+    case 0: C = grad_matrix<0>(Xx, Yx, Xf, Yf); break;
+    case 1: C = grad_matrix<1>(Xx, Yx, Xf, Yf); break;
+    case 2: C = grad_matrix<2>(Xx, Yx, Xf, Yf); break;
+    default: C = grad_matrix<3>(Xx, Yx, Xf, Yf); break;
+  }
+  const double sc = 2.0 * kappa * sign;
+  double2* out = G + ((size_t)s * 4 + mu) * 9;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) out[k] = make_double2(sc * C.m[k].re, -sc * C.m[k].im);
+}
+
+// out[0] = sum_x Re phi(x)^dag X(x)
+__global__ void __launch_bounds__(kBS) dot_re_kernel(int V, SpinorRef a, SpinorRef b, ReduceScratch rs,
+                                                     double* out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  double red[1] = {0.0};
+  if (s < V) {
+    cplx<double> u[12], v[12];
+    load_spinor<SStore::F64, double>(a, V, s, u);
+    load_spinor<SStore::F64, double>(b, V, s, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) red[0] += u[k].re * v[k].re + u[k].im * v[k].im;
+  }
+  double tot[1];
+  if (grid_sum<1>(red, rs, tot)) out[0] = tot[0];
+}
+
+void launch_fermion_grad(const Geom& g, SpinorRef X, SpinorRef Y, double* G, double kappa, cudaStream_t st) {
+  fermion_grad_kernel<<<grid_for(4 * g.V, kBS), kBS, 0, st>>>(g, X, Y, reinterpret_cast<double2*>(G), kappa);
+}
+void launch_dot_re(const Geom& g, SpinorRef a, SpinorRef b, const ReduceScratch& rs, double* out, cudaStream_t st) {
+  dot_re_kernel<<<grid_for(g.V, kBS), kBS, 0, st>>>(g.V, a, b, rs, out);
+}
+
 void launch_fermion_force(const Geom& g, const void* gauge, SpinorRef X, SpinorRef Y, double* f, double kappa,
                           double eps, bool update, cudaStream_t st) {
   const int grid = grid_for(4 * g.V, kBS);

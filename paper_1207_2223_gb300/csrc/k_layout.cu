@@ -5,6 +5,16 @@
 
 namespace lq {
 
+int resident_grid(const void* kernel, int block) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
+  if (sms <= 0) sms = 1;
+  if (per_sm <= 0) per_sm = 1;
+  return sms * per_sm;
+}
+
 size_t spinor_bytes(SStore s, int V) {
   switch (s) {
     case SStore::F64: return (size_t)V * 24 * 8;

@@ -135,6 +135,31 @@ __device__ __forceinline__ void load_spinor(const SpinorRef& f, int V, int s, cp
   }
 }
 
+// Load without applying the per-site norm of 16-bit formats; returns the
+// norm (1 for FP32 / FP64).  The stencil applies it to the projected half
+// spinor, half as many multiplications as scaling all 24 reals.
+template <SStore S, typename T>
+__device__ __forceinline__ T load_spinor_raw(const SpinorRef& f, int V, int s, cplx<T> v[12]) {
+  if constexpr (S == SStore::F64 || S == SStore::F32) {
+    load_spinor<S, T>(f, V, s, v);
+    return (T)1;
+  } else {
+    using H = typename SpinorTraits<S>::half_t;
+    const uint4* p = static_cast<const uint4*>(f.p);
+    const float nrm = __ldg(f.norm + s);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 w = __ldg(p + (size_t)k * V + s);
+      float2 a = HalfOps<H>::to2(w.x), b = HalfOps<H>::to2(w.y), c = HalfOps<H>::to2(w.z), e = HalfOps<H>::to2(w.w);
+      v[4 * k + 0] = {(T)a.x, (T)a.y};
+      v[4 * k + 1] = {(T)b.x, (T)b.y};
+      v[4 * k + 2] = {(T)c.x, (T)c.y};
+      v[4 * k + 3] = {(T)e.x, (T)e.y};
+    }
+    return (T)nrm;
+  }
+}
+
 template <SStore S, typename T>
 __device__ __forceinline__ void store_spinor(const SpinorRef& f, int V, int s, const cplx<T> v[12]) {
   if constexpr (S == SStore::F64) {

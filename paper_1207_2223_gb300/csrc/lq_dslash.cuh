@@ -13,6 +13,8 @@
 // to the result is an epilogue functor, so the CG vector updates and the
 // FP64 norms fuse into the same pass over the lattice.
 #pragma once
+#include <algorithm>
+
 #include "lq_device.cuh"
 
 namespace lq {
@@ -50,12 +52,13 @@ __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, cons
   {
     const int n = nbr_fwd(geo, s, c, MU);
     cplx<T> p[12];
-    load_spinor<SI, T>(in, geo.V, n, p);
+    T sc = load_spinor_raw<SI, T>(in, geo.V, n, p);
     cplx<T> h0[3], h1[3];
     project<MU, SF>(p, h0, h1);
-    if (MU == 3 && geo.antiperiodic && c[3] == geo.L[3] - 1) {
+    if (MU == 3 && geo.antiperiodic && c[3] == geo.L[3] - 1) sc = -sc;
+    if (SI == SStore::F16 || SI == SStore::BF16 || (MU == 3 && geo.antiperiodic)) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) { h0[k] = -h0[k]; h1[k] = -h1[k]; }
+      for (int k = 0; k < 3; ++k) { h0[k] = sc * h0[k]; h1[k] = sc * h1[k]; }
     }
     cplx<T> u[9];
     load_link<G, T>(U, geo.V, MU, s, u);
@@ -67,12 +70,13 @@ __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, cons
   {
     const int n = nbr_bwd(geo, s, c, MU);
     cplx<T> p[12];
-    load_spinor<SI, T>(in, geo.V, n, p);
+    T sc = load_spinor_raw<SI, T>(in, geo.V, n, p);
     cplx<T> h0[3], h1[3];
     project<MU, -SF>(p, h0, h1);
-    if (MU == 3 && geo.antiperiodic && c[3] == 0) {
+    if (MU == 3 && geo.antiperiodic && c[3] == 0) sc = -sc;
+    if (SI == SStore::F16 || SI == SStore::BF16 || (MU == 3 && geo.antiperiodic)) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) { h0[k] = -h0[k]; h1[k] = -h1[k]; }
+      for (int k = 0; k < 3; ++k) { h0[k] = sc * h0[k]; h1[k] = sc * h1[k]; }
     }
     cplx<T> u[9];
     load_link<G, T>(U, geo.V, MU, n, u);
@@ -83,15 +87,38 @@ __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, cons
   }
 }
 
+// Threads per block: 256 for FP32 arithmetic; 128 for FP64, whose ~140
+// registers per thread would otherwise leave one block per SM.
+template <typename T> struct DslashBlock { static constexpr int value = 256; };
+template <> struct DslashBlock<double> { static constexpr int value = 128; };
+// Minimum resident blocks per SM requested from the compiler (register cap).
+#ifndef LQ_DSLASH_MIN_BLOCKS
+#define LQ_DSLASH_MIN_BLOCKS 2
+#endif
+
+// |v|^2 of one site in the kernel's arithmetic precision; the per-site sums
+// are then accumulated in FP64 (one FP64 add per site: the FP64 pipe of this
+// part is ~60x slower than its FP32 pipe).
+template <typename T>
+__device__ __forceinline__ double site_norm2(const cplx<T> v[12]) {
+  T a = (T)0;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) { a = fma(v[k].re, v[k].re, a); a = fma(v[k].im, v[k].im, a); }
+  return (double)a;
+}
+
+// Grid-stride: the grid is one wave of resident blocks and every thread
+// walks the lattice in steps of the grid size, so the halt check and the
+// block reduction happen once per block rather than once per 256 sites.
 template <typename T, GStore G, SStore SI, bool DAG, class Epi>
-__global__ void __launch_bounds__(256) dslash_kernel(Geom geo, GaugeRef U, SpinorRef in, T kappa, Epi epi,
-                                                      ReduceScratch rs) {
+__global__ void __launch_bounds__(DslashBlock<T>::value, LQ_DSLASH_MIN_BLOCKS) dslash_kernel(Geom geo, GaugeRef U, SpinorRef in,
+                                                                        T kappa, Epi epi, ReduceScratch rs) {
   if (epi.halted()) return;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
   double red[Epi::NRED];
 #pragma unroll
   for (int q = 0; q < Epi::NRED; ++q) red[q] = 0.0;
-  if (s < geo.V) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < geo.V; s += stride) {
     int c[4];
     site_coords(geo, s, c);
     cplx<T> acc[12];
@@ -138,10 +165,7 @@ struct EpiStoreNorm {                   // out = M psi, *result = |out|^2
   __device__ bool halted() const { return false; }
   template <typename T> __device__ void apply(int V, int s, cplx<T> v[12], double (&red)[NRED]) const {
     store_spinor<SO, T>(out, V, s, v);
-    double a = 0.0;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) a += (double)v[k].re * (double)v[k].re + (double)v[k].im * (double)v[k].im;
-    red[0] += a;
+    red[0] += site_norm2(v);
   }
   __device__ void finalize(double (&tot)[NRED]) const { *result = tot[0]; }
 };
@@ -156,10 +180,7 @@ struct EpiCG1 {
   __device__ bool halted() const { return *(volatile const int*)&st->halt; }
   template <typename T> __device__ void apply(int V, int s, cplx<T> v[12], double (&red)[NRED]) const {
     store_spinor<ST, T>(t, V, s, v);
-    double a = 0.0;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) a += (double)v[k].re * (double)v[k].re + (double)v[k].im * (double)v[k].im;
-    red[0] += a;
+    red[0] += site_norm2(v);
   }
   __device__ void finalize(double (&tot)[NRED]) const {
     const double tt = tot[0];
@@ -190,18 +211,16 @@ struct EpiCG2 {
     load_spinor<SR, T, false>(r, V, s, rv);
     load_spinor<SX, T, false>(x, V, s, xv);
     load_spinor<SP, T>(p, V, s, pv);
-    double a = 0.0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       rv[k].re = fma(-alpha, v[k].re, rv[k].re);
       rv[k].im = fma(-alpha, v[k].im, rv[k].im);
       xv[k].re = fma(alpha, pv[k].re, xv[k].re);
       xv[k].im = fma(alpha, pv[k].im, xv[k].im);
-      a += (double)rv[k].re * (double)rv[k].re + (double)rv[k].im * (double)rv[k].im;
     }
     store_spinor<SR, T>(r, V, s, rv);
     store_spinor<SX, T>(x, V, s, xv);
-    red[0] += a;
+    red[0] += site_norm2(rv);
   }
   __device__ void finalize(double (&tot)[NRED]) const {
     const double rr_new = tot[0];
@@ -248,11 +267,16 @@ struct EpiResidual {
 
 inline int grid_for(int V, int bs) { return (V + bs - 1) / bs; }
 
+// Resident blocks of one kernel on the current device (queried once per kernel).
+int resident_grid(const void* kernel, int block);
+
 template <typename T, GStore G, SStore SI, bool DAG, class Epi>
 inline void launch_dslash(const Geom& geo, GaugeRef U, SpinorRef in, double kappa, const Epi& epi,
                           const ReduceScratch& rs, cudaStream_t stream) {
-  const int bs = 256;
-  dslash_kernel<T, G, SI, DAG, Epi><<<grid_for(geo.V, bs), bs, 0, stream>>>(geo, U, in, (T)kappa, epi, rs);
+  constexpr int bs = DslashBlock<T>::value;
+  static const int wave = resident_grid(reinterpret_cast<const void*>(&dslash_kernel<T, G, SI, DAG, Epi>), bs);
+  const int grid = std::min(grid_for(geo.V, bs), wave);
+  dslash_kernel<T, G, SI, DAG, Epi><<<grid, bs, 0, stream>>>(geo, U, in, (T)kappa, epi, rs);
 }
 
 }  // namespace lq

@@ -113,6 +113,9 @@ void launch_accumulate_x(const Geom& g, SStore slo, SpinorRef xlo, SpinorRef xhi
 // after a true-residual pass: beta = rr_true / rr_prev (0 when restart), rr = rr_ref = rr_true, resume
 void launch_state_after_residual(SolverState* st, int restart, cudaStream_t stream);
 void launch_zero_spinor(const Geom& g, SStore s, SpinorRef f, cudaStream_t stream);
+// x = 0, r = p = src64 in format s (restart of the inner iteration)
+void launch_inner_restart(const Geom& g, SpinorRef src64, SStore s, SpinorRef x, SpinorRef r, SpinorRef p,
+                          cudaStream_t stream);
 
 // ---- Wilson operator applications (k_apply.cu): out = M in or M^dag in
 void apply_M_prec(const Geom& g, int prec, const void* gauge, SpinorRef in, SpinorRef out, double kappa,
@@ -124,6 +127,13 @@ void cg64_true_residual(lq_ctx* c, double kappa, int store_lo_prec, cudaStream_t
 
 // ---- low-precision CG iteration (k_cglo.cu)
 void cglo_iteration(lq_ctx* c, int prec, double kappa, cudaStream_t stream);
+// single steps (which = 1: t = M p with |t|^2; 2: r -= alpha M^dag t, x += alpha p, |r|^2)
+void cg64_step(lq_ctx* c, int which, double kappa, cudaStream_t stream);
+void cglo_step(lq_ctx* c, int prec, int which, double kappa, cudaStream_t stream);
+inline void cg_step(lq_ctx* c, int prec, int which, double kappa, cudaStream_t stream) {
+  if (prec == LQ_F64) cg64_step(c, which, kappa, stream);
+  else cglo_step(c, prec, which, kappa, stream);
+}
 
 }  // namespace lq
 
@@ -141,6 +151,8 @@ void launch_kinetic_diff(const Geom& g, const double* p, const double* p0, const
 // ---- fermion side (k_force.cu)
 void launch_fermion_force(const Geom& g, const void* gauge, SpinorRef X, SpinorRef Y, double* f, double kappa,
                           double eps, bool update, cudaStream_t st);
+void launch_fermion_grad(const Geom& g, SpinorRef X, SpinorRef Y, double* G, double kappa, cudaStream_t st);
+void launch_dot_re(const Geom& g, SpinorRef a, SpinorRef b, const ReduceScratch& rs, double* out, cudaStream_t st);
 void launch_fermion_action_diff(const Geom& g, SpinorRef phi, SpinorRef X, SpinorRef chi, const ReduceScratch& rs,
                                 double* out, cudaStream_t st);
 }  // namespace lq

@@ -27,7 +27,7 @@ class LQError(RuntimeError):
 class lq_solve_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("converged", ctypes.c_int), ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("escalations", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -68,11 +68,14 @@ SIGNATURES = {
     "lq_solve_MdagM": (_I, [_P, _P, _P, _D, _D, _I, _I, _I, _P, _I, ctypes.POINTER(lq_solve_stats)]),
     "lq_time_dslash": (_I, [_P, _P, _D, _I, _I, _I, _I, ctypes.POINTER(_D)]),
     "lq_apply_MdagM_static": (_I, [_P, _P, _P, ctypes.POINTER(_I), _I, _D, _P]),
+    "lq_time_cg_kernel": (_I, [_P, _P, _D, _I, _I, _I, ctypes.POINTER(_D)]),
     "lq_plaquette": (_I, [_P, ctypes.POINTER(_D)]),
     "lq_gauge_action": (_I, [_P, _D, ctypes.POINTER(_D)]),
     "lq_gauge_force": (_I, [_P, _P, _D]),
     "lq_fermion_force": (_I, [_P, _P, _P, _D]),
     "lq_link_update": (_I, [_P, _P, _D]),
+    "lq_fermion_grad": (_I, [_P, _P, _P, _D]),
+    "lq_pseudofermion_action": (_I, [_P, _P, _D, _D, _I, _I, _I, ctypes.POINTER(_D), _P]),
     "lq_hmc_trajectory": (_I, [_P, ctypes.POINTER(lq_hmc_params), _P, _P, _D, ctypes.POINTER(lq_traj_result)]),
 }
 
@@ -189,6 +192,14 @@ def lq_time_dslash(ctx, inp, kappa, dagger=False, prec=LQ_F64, n=20, flush_l2=Fa
     return ms.value
 
 
+def lq_time_cg_kernel(ctx, inp, kappa, which=0, prec=LQ_F64, n=20):
+    """Average device milliseconds of a CG iteration (which=0) or one of its passes (1, 2, 3)."""
+    ms = _D()
+    _check(ctx, load().lq_time_cg_kernel(ctx, _ptr(inp), float(kappa), int(which), int(prec), int(n),
+                                         ctypes.byref(ms)))
+    return ms.value
+
+
 def lq_plaquette(ctx):
     v = _D()
     _check(ctx, load().lq_plaquette(ctx, ctypes.byref(v)))
@@ -207,6 +218,18 @@ def lq_gauge_force(ctx, F, beta):
 
 def lq_fermion_force(ctx, F, X, kappa):
     _check(ctx, load().lq_fermion_force(ctx, _ptr(F), _ptr(X), float(kappa)))
+
+
+def lq_fermion_grad(ctx, G, X, kappa):
+    _check(ctx, load().lq_fermion_grad(ctx, _ptr(G), _ptr(X), float(kappa)))
+
+
+def lq_pseudofermion_action(ctx, phi, kappa, tol=1e-10, maxiter=100000, inner_prec=LQ_F64, reliable_every=50,
+                            X=None):
+    v = _D()
+    _check(ctx, load().lq_pseudofermion_action(ctx, _ptr(phi), float(kappa), float(tol), int(maxiter),
+                                               int(inner_prec), int(reliable_every), ctypes.byref(v), _ptr(X)))
+    return v.value
 
 
 def lq_link_update(ctx, p, eps):
