@@ -149,6 +149,28 @@ lq_status lq_solve_MdagM(lq_ctx* ctx, double* x, const double* phi, double kappa
                          int inner_prec, int reliable_every, double* hist, int hist_len,
                          lq_solve_stats* stats);
 
+/* Batched CG: n independent systems solved together, one launch per CG pass
+ * (the CG routine of Sec. 3 over a batch).  System k is the lattice and gauge
+ * field of ctxs[k] (volumes and kappa[k] may differ; all contexts on one
+ * device) with nrhs right-hand sides phi[k] (device, canonical spinors stored
+ * one after another: [nrhs][V_k][4][3] complex), solution x[k] (device, same
+ * layout).  Right-hand sides of one system share its links, which are read
+ * once per site for all of them.  Iterations run in FP32 (inner_prec LQ_F32
+ * or LQ_F32_12) with FP64 reliable updates every reliable_every iterations;
+ * a column (system x right-hand side) whose FP64 true residual meets tol is
+ * frozen.  1 <= n <= 16, 1 <= nrhs <= 16, n * nrhs <= 64.  Block size is
+ * picked by timing candidates on the first call (autotuning); the iterations
+ * run as CUDA graphs on ctxs[0]'s stream, which owns the workspace.
+ *   hist     optional host array [n * nrhs][hist_len]: relative iterated residual
+ *            of every column per iteration
+ *   iters    optional host int[n * nrhs]: iterations until each column was frozen
+ *   resid    optional host double[n * nrhs]: final FP64 true relative residuals
+ * Synchronises.  Errors: LQ_ERR_ARG (host buffers, sizes), LQ_ERR_STATE,
+ * LQ_ERR_NOT_CONVERGED, LQ_ERR_NAN, LQ_ERR_CUDA (message on ctxs[0]). */
+lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const double** phi, const double* kappa, int nrhs,
+                         double tol, int maxiter, int inner_prec, int reliable_every, double* hist, int hist_len,
+                         int* iters, double* resid, lq_solve_stats* stats);
+
 /* ---------------------------------------------------------------- MD */
 
 /* Parameters of one HMC trajectory (Sec. 3, the three steps of the evolution). */

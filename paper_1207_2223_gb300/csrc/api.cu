@@ -404,6 +404,7 @@ lq_status lq_create(lq_ctx** out, const int dims[4], int t_antiperiodic, void* c
 lq_status lq_destroy(lq_ctx* c) {
   if (!c) return LQ_OK;
   cudaStreamSynchronize(c->stream);
+  destroy_batch_work(c->batch);
   for (auto& kv : c->graphs)
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
@@ -808,7 +809,6 @@ lq_status lq_time_cg_kernel(lq_ctx* c, const double* in, double kappa, int which
   const int k = (int)s;
   Field& r = lo ? c->r_lo[k] : c->r64;
   Field& p = lo ? c->p_lo[k] : c->p64;
-  Field& t = lo ? c->t_lo[k] : c->t64;
   Field& x = lo ? c->x_lo[k] : c->x64;
   const double* din = nullptr;
   LQ_TRY(stage_spinor_in(c, in, &din));

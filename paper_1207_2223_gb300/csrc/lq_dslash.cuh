@@ -45,14 +45,30 @@ struct SolverState {
 
 struct NoEpiState {};
 
-template <int MU, bool DAG, GStore G, SStore SI, typename T>
+// Where the spinor of site n lives: one field of V sites (Single), or one
+// system of a batch whose right-hand sides are interleaved fastest inside a
+// field shared by all systems (Batched: element off + n R + r, chunk stride
+// = the batch's total number of elements).
+struct SingleIndex {
+  int V;
+  __device__ __forceinline__ int stride() const { return V; }
+  __device__ __forceinline__ int operator()(int n) const { return n; }
+};
+struct BatchIndex {
+  int total, off, R, r;
+  __device__ __forceinline__ int stride() const { return total; }
+  __device__ __forceinline__ int operator()(int n) const { return off + n * R + r; }
+};
+
+template <int MU, bool DAG, GStore G, SStore SI, typename T, class IX = SingleIndex>
 __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, const SpinorRef& in, int s,
-                                        const int c[4], cplx<T> acc[12]) {
+                                        const int c[4], cplx<T> acc[12], IX ix = IX{0}) {
+  if constexpr (std::is_same<IX, SingleIndex>::value) ix.V = geo.V;
   constexpr int SF = DAG ? +1 : -1;   // forward hop uses (1 + SF g_mu)
   {
     const int n = nbr_fwd(geo, s, c, MU);
     cplx<T> p[12];
-    T sc = load_spinor_raw<SI, T>(in, geo.V, n, p);
+    T sc = load_spinor_raw<SI, T>(in, ix.stride(), ix(n), p);
     cplx<T> h0[3], h1[3];
     project<MU, SF>(p, h0, h1);
     if (MU == 3 && geo.antiperiodic && c[3] == geo.L[3] - 1) sc = -sc;
@@ -70,7 +86,7 @@ __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, cons
   {
     const int n = nbr_bwd(geo, s, c, MU);
     cplx<T> p[12];
-    T sc = load_spinor_raw<SI, T>(in, geo.V, n, p);
+    T sc = load_spinor_raw<SI, T>(in, ix.stride(), ix(n), p);
     cplx<T> h0[3], h1[3];
     project<MU, -SF>(p, h0, h1);
     if (MU == 3 && geo.antiperiodic && c[3] == 0) sc = -sc;

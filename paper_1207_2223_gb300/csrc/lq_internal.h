@@ -90,9 +90,13 @@ struct lq_ctx {
   double* dscalar_host = nullptr;        // pinned mirror [8]
 
   std::map<std::tuple<int, int, int, double>, lq::GraphEntry> graphs;
+  void* batch = nullptr;                 // workspace of lq_solve_batch (k_batch.cu)
 };
 
 namespace lq {
+
+// ---- batched solves (k_batch.cu)
+void destroy_batch_work(void* w);
 
 // ---- layout (k_layout.cu)
 void launch_pack_gauge64(const Geom& g, const double* canon, void* soa, cudaStream_t st);

@@ -69,6 +69,8 @@ SIGNATURES = {
     "lq_time_dslash": (_I, [_P, _P, _D, _I, _I, _I, _I, ctypes.POINTER(_D)]),
     "lq_apply_MdagM_static": (_I, [_P, _P, _P, ctypes.POINTER(_I), _I, _D, _P]),
     "lq_time_cg_kernel": (_I, [_P, _P, _D, _I, _I, _I, ctypes.POINTER(_D)]),
+    "lq_solve_batch": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_D), _I,
+                            _D, _I, _I, _I, _P, _I, _P, _P, ctypes.POINTER(lq_solve_stats)]),
     "lq_plaquette": (_I, [_P, ctypes.POINTER(_D)]),
     "lq_gauge_action": (_I, [_P, _D, ctypes.POINTER(_D)]),
     "lq_gauge_force": (_I, [_P, _P, _D]),
@@ -198,6 +200,27 @@ def lq_time_cg_kernel(ctx, inp, kappa, which=0, prec=LQ_F64, n=20):
     _check(ctx, load().lq_time_cg_kernel(ctx, _ptr(inp), float(kappa), int(which), int(prec), int(n),
                                          ctypes.byref(ms)))
     return ms.value
+
+
+def lq_solve_batch(ctxs, xs, phis, kappas, nrhs=1, tol=1e-10, maxiter=100000, inner_prec=LQ_F32_12,
+                   reliable_every=50, hist_len=0):
+    """Solve n systems together.  Returns (status, stats, iters[n*nrhs], resid[n*nrhs], hist or None)."""
+    import numpy as np
+    n = len(ctxs)
+    c_arr = (_P * n)(*[c.value if hasattr(c, "value") else c for c in ctxs])
+    x_arr = (_P * n)(*[_ptr(x) for x in xs])
+    p_arr = (_P * n)(*[_ptr(p) for p in phis])
+    k_arr = (_D * n)(*[float(k) for k in kappas])
+    iters = np.zeros(n * nrhs, dtype=np.int32)
+    resid = np.zeros(n * nrhs)
+    hist = np.zeros((n * nrhs, hist_len)) if hist_len > 0 else None
+    st = lq_solve_stats()
+    status = load().lq_solve_batch(c_arr, n, x_arr, p_arr, k_arr, int(nrhs), float(tol), int(maxiter),
+                                   int(inner_prec), int(reliable_every), _ptr(hist), int(hist_len),
+                                   iters.ctypes.data, resid.ctypes.data, ctypes.byref(st))
+    if status not in (LQ_OK, LQ_ERR_NOT_CONVERGED):
+        _check(ctxs[0], status)
+    return status, st.as_dict(), iters, resid, hist
 
 
 def lq_plaquette(ctx):

@@ -1,0 +1,155 @@
+"""Batched CG (many right-hand sides sharing one gauge field; independent lattices of
+different volumes and kappa in one launch) against the oracle and the single solver."""
+import numpy as np
+import pytest
+
+from oracle.cg import cg_MdagM
+from synth import Lattice, gauge_exp_iA, source
+from tests.gpu_common import require_gpu, dev, host, rel_err, torch
+
+pytestmark = pytest.mark.gpu
+
+X_TOL = 1e-6     # conditioning bound of the solution error at a 1e-10 residual (see test_gpu_solver)
+
+
+@pytest.fixture(scope="module")
+def lq():
+    return require_gpu()
+
+
+def _true_residuals(lq, dims, U, xs, phis, kappa):
+    ctx = lq.lq_create(dims)
+    try:
+        lq.lq_gauge_set(ctx, U)
+        out = []
+        for x, phi in zip(xs, phis):
+            r = torch.empty_like(x)
+            lq.lq_apply_MdagM(ctx, r, x, kappa, lq.LQ_F64)
+            out.append(float(torch.linalg.vector_norm(phi - r) / torch.linalg.vector_norm(phi)))
+        return out
+    finally:
+        lq.lq_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_multi_rhs_matches_oracle(lq, prec):
+    dims, R, kappa = (4, 4, 4, 4), 12, 0.155
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, 0.3, 3)
+    phis = np.stack([source(lat, 3, i) for i in range(R)])            # [R][V][4][3]
+    ctx = lq.lq_create(dims)
+    try:
+        lq.lq_gauge_set(ctx, dev(U))
+        phid = dev(phis)
+        x = torch.zeros_like(phid)
+        status, st, iters, resid, hist = lq.lq_solve_batch([ctx], [x], [phid], [kappa], R, 1e-10, 5000, prec, 25,
+                                                           hist_len=3000)
+        xs = host(x)
+    finally:
+        lq.lq_destroy(ctx)
+    assert status == lq.LQ_OK and st["converged"] == 1
+    assert np.all(resid <= 1e-10) and np.all(iters > 0)
+    res = _true_residuals(lq, dims, dev(U), [dev(xs[i]) for i in range(R)], [dev(phis[i]) for i in range(R)], kappa)
+    assert max(res) <= 1e-10
+    for i in (0, 5, 11):
+        xr, _, _ = cg_MdagM(U, phis[i], dims, kappa, 1e-13)
+        assert rel_err(xs[i], xr) < X_TOL
+    n = st["iterations"]
+    assert np.all(hist[:, 0] > 0) and np.all(hist[:, :n].min(axis=1) < 1e-6)
+
+
+def test_uneven_lattices_one_launch_match_oracle(lq):
+    shapes = [(4, 4, 4, 4), (2, 4, 6, 4), (6, 2, 2, 4), (4, 4, 2, 8)]
+    kappas = [0.12, 0.14, 0.15, 0.155]
+    ctxs, xs, phis, Us = [], [], [], []
+    try:
+        for k, (dims, kap) in enumerate(zip(shapes, kappas)):
+            lat = Lattice(dims)
+            U = gauge_exp_iA(lat, 0.3, 4 + k)
+            c = lq.lq_create(dims)
+            lq.lq_gauge_set(c, dev(U))
+            ctxs.append(c)
+            Us.append(U)
+            phis.append(dev(source(lat, 4 + k)))
+            xs.append(torch.zeros_like(phis[-1]))
+        status, st, iters, resid, _ = lq.lq_solve_batch(ctxs, xs, phis, kappas, 1, 1e-10, 5000, lq.LQ_F32_12, 50)
+        got = [host(x) for x in xs]
+    finally:
+        for c in ctxs:
+            lq.lq_destroy(c)
+    assert status == lq.LQ_OK and np.all(resid <= 1e-10)
+    for k, (dims, kap) in enumerate(zip(shapes, kappas)):
+        xr, _, _ = cg_MdagM(Us[k], host(phis[k]), dims, kap, 1e-13)
+        assert rel_err(got[k], xr) < X_TOL, dims
+    # the lightest system (kappa 0.12) is frozen no later than the heaviest (kappa 0.155)
+    assert iters[0] <= iters[3]
+
+
+def test_batch_reuses_workspace_and_rejects_bad_arguments(lq):
+    dims = (4, 4, 2, 4)
+    lat = Lattice(dims)
+    ctx = lq.lq_create(dims)
+    try:
+        lq.lq_gauge_set(ctx, dev(gauge_exp_iA(lat, 0.3, 1)))
+        phi = dev(np.stack([source(lat, 1, i) for i in range(2)]))
+        x1, x2 = torch.zeros_like(phi), torch.zeros_like(phi)
+        s1 = lq.lq_solve_batch([ctx], [x1], [phi], [0.15], 2)
+        s2 = lq.lq_solve_batch([ctx], [x2], [phi], [0.15], 2)
+        assert s1[0] == s2[0] == lq.LQ_OK
+        assert torch.equal(x1, x2)                         # deterministic reductions
+        with pytest.raises(lq.LQError):
+            lq.lq_solve_batch([ctx], [host(x1)], [phi], [0.15], 2)   # host buffer
+        with pytest.raises(lq.LQError):
+            lq.lq_solve_batch([ctx], [x1], [phi], [0.15], 2, inner_prec=lq.LQ_F16_12)
+    finally:
+        lq.lq_destroy(ctx)
+
+
+def test_full_size_multi_rhs_24x24x24x24(lq):
+    """24^4, kappa 0.155, seed 3, 12 right-hand sides sharing one FP32 gauge field: every
+    column reaches a 1e-10 FP64 true residual and agrees with the single-RHS solver."""
+    dims, R, kappa = (24, 24, 24, 24), 12, 0.155
+    lat = Lattice(dims)
+    U = dev(gauge_exp_iA(lat, 0.3, 3))
+    phis = dev(np.stack([source(lat, 3, i) for i in range(R)]))
+    ctx = lq.lq_create(dims)
+    try:
+        lq.lq_gauge_set(ctx, U)
+        x = torch.zeros_like(phis)
+        status, st, iters, resid, hist = lq.lq_solve_batch([ctx], [x], [phis], [kappa], R, 1e-10, 20000,
+                                                           lq.LQ_F32, 50, hist_len=4000)
+        assert status == lq.LQ_OK and np.all(resid <= 1e-10)
+        for i in (0, 7):
+            r = torch.empty_like(x[i])
+            lq.lq_apply_MdagM(ctx, r, x[i], kappa, lq.LQ_F64)
+            assert float(torch.linalg.vector_norm(phis[i] - r) / torch.linalg.vector_norm(phis[i])) <= 1e-10
+            xs = torch.zeros_like(phis[i])
+            lq.lq_solve_MdagM(ctx, xs, phis[i], kappa, 1e-10, 20000, lq.LQ_F32_12, 50)
+            assert float(torch.linalg.vector_norm(xs - x[i]) / torch.linalg.vector_norm(xs)) < X_TOL
+    finally:
+        lq.lq_destroy(ctx)
+
+
+def test_full_size_uneven_lattices(lq):
+    """8^4, 12^4, 16^4 and 8^3 x 16 with kappa 0.12, 0.14, 0.15, 0.155 and seeds 4-7, one batch."""
+    shapes = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (8, 8, 8, 16)]
+    kappas = [0.12, 0.14, 0.15, 0.155]
+    ctxs, xs, phis = [], [], []
+    try:
+        for k, dims in enumerate(shapes):
+            lat = Lattice(dims)
+            c = lq.lq_create(dims)
+            lq.lq_gauge_set(c, dev(gauge_exp_iA(lat, 0.3, 4 + k)))
+            ctxs.append(c)
+            phis.append(dev(source(lat, 4 + k)))
+            xs.append(torch.zeros_like(phis[-1]))
+        status, st, iters, resid, hist = lq.lq_solve_batch(ctxs, xs, phis, kappas, 1, 1e-10, 20000, lq.LQ_F32_12,
+                                                           50, hist_len=4000)
+        assert status == lq.LQ_OK and np.all(resid <= 1e-10)
+        for k in range(4):
+            r = torch.empty_like(xs[k])
+            lq.lq_apply_MdagM(ctxs[k], r, xs[k], kappas[k], lq.LQ_F64)
+            assert float(torch.linalg.vector_norm(phis[k] - r) / torch.linalg.vector_norm(phis[k])) <= 1e-10
+    finally:
+        for c in ctxs:
+            lq.lq_destroy(c)
