@@ -137,6 +137,85 @@ def oracle_cg_iteration_seconds(U, phi, site_fraction=1):
     return (t1 - t0) * site_fraction + (t2 - t1)
 
 
+def measure_extras(lq, torch, dev):
+    """Numbers beside the headline, each measured once outside the timed region:
+    HMC trajectories at 16^4, the batched solve at 24^4 x 12, and CG time against
+    iteration count with and without CUDA graphs (per-call overhead = intercept)."""
+    import numpy as np
+    from synth import Lattice, gauge_exp_iA, source, momenta, chi_noise, metropolis_uniform
+    out = {}
+    # HMC: 16^4, beta 5.6, kappa 0.155, 20 leapfrog steps, tau 1, reunitarised exp(iA) start
+    dims = (16, 16, 16, 16)
+    lat = Lattice(dims)
+    U = torch.from_numpy(gauge_exp_iA(lat, 0.3, 1, reunitarise=True)).to(dev)
+    p0 = torch.from_numpy(momenta(lat, 1)).to(dev)
+    chi = torch.from_numpy(chi_noise(lat, 1)).to(dev)
+    u = metropolis_uniform(1)
+    hmc = {}
+    for name, prec in (("f64", lq.LQ_F64), ("mixed_f32_12", lq.LQ_F32_12)):
+        ctx = lq.lq_create(dims, True, torch.cuda.current_stream(dev).cuda_stream)
+        try:
+            lq.lq_gauge_set(ctx, U)
+            r = lq.lq_hmc_trajectory(ctx, p0.clone(), chi, u, 5.6, 0.155, 20, 1.0, 1e-10, 20000, prec, 50)
+        finally:
+            lq.lq_destroy(ctx)
+        hmc[name] = {"seconds": r["seconds"], "trajectories_per_s": 1.0 / r["seconds"], "dH": r["dH"],
+                     "accepted": r["accepted"], "solves": r["solves"], "cg_iterations": r["cg_iterations"],
+                     "plaquette": r["plaquette"]}
+    out["hmc_16x16x16x16"] = hmc
+    # batched solve: 24^4, kappa 0.155, seed 3, 12 right-hand sides sharing one gauge field
+    dims = (24, 24, 24, 24)
+    lat = Lattice(dims)
+    U = torch.from_numpy(gauge_exp_iA(lat, 0.3, 3)).to(dev)
+    phis = torch.from_numpy(np.stack([source(lat, 3, i) for i in range(12)])).to(dev)
+    ctx = lq.lq_create(dims, True, torch.cuda.current_stream(dev).cuda_stream)
+    try:
+        lq.lq_gauge_set(ctx, U)
+        x = torch.zeros_like(phis)
+        lq.lq_solve_batch([ctx], [x], [phis], [0.155], 12, 1e-10, 20000, lq.LQ_F32_12, 50)   # autotune
+        t0 = time.perf_counter()
+        status, st, iters, resid, _ = lq.lq_solve_batch([ctx], [x], [phis], [0.155], 12, 1e-10, 20000,
+                                                        lq.LQ_F32_12, 50)
+        tb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for i in range(12):
+            xs = torch.zeros_like(phis[i])
+            lq.lq_solve_MdagM(ctx, xs, phis[i], 0.155, 1e-10, 20000, lq.LQ_F32_12, 50)
+        ts = time.perf_counter() - t0
+    finally:
+        lq.lq_destroy(ctx)
+    out["batch_24x24x24x24_12rhs"] = {"seconds": tb, "sequential_seconds": ts, "iterations": st["iterations"],
+                                      "max_true_rel_resid": float(resid.max())}
+    # CG time against iteration count, FP64 CG stopped by the iteration limit (tol 1e-30),
+    # with and without CUDA graphs; 8^4 (launch-bound) and 16^4
+    for dims in ((8, 8, 8, 8), (16, 16, 16, 16)):
+        lat = Lattice(dims)
+        U = torch.from_numpy(gauge_exp_iA(lat, 0.3, 1)).to(dev)
+        phi = torch.from_numpy(source(lat, 1)).to(dev)
+        scan = {}
+        for graphs in (1, 0):
+            ctx = lq.lq_create(dims, True, torch.cuda.current_stream(dev).cuda_stream)
+            try:
+                lq.lq_gauge_set(ctx, U)
+                lq.lq_set_option(ctx, lq.LQ_OPT_CUDA_GRAPHS, graphs)
+                pts = []
+                for n in (16, 64, 128, 256, 16, 64, 128, 256):
+                    x = torch.zeros_like(phi)
+                    t0 = time.perf_counter()
+                    lq.lq_solve_MdagM(ctx, x, phi, 0.155, 1e-30, n, lq.LQ_F64, 0)
+                    pts.append((n, time.perf_counter() - t0))
+                pts = pts[4:]
+                ns = np.array([q[0] for q in pts], dtype=float)
+                ts = np.array([q[1] for q in pts])
+                slope, icpt = np.polyfit(ns, ts, 1)
+            finally:
+                lq.lq_destroy(ctx)
+            scan["graphs" if graphs else "no_graphs"] = {"seconds_per_iteration": slope, "intercept_s": icpt,
+                                                         "points": [[int(a), b] for a, b in pts]}
+        out["cg_time_vs_iterations_%dx%dx%dx%d" % dims] = scan
+    return out
+
+
 def run_reference(args):
     import numpy as np
     rank, size = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
@@ -283,6 +362,8 @@ def run_ours(args):
         e2e = {"value": e2e_units / e2e_t, "unit": "solves/s", "h2d_bytes_per_step": int(U.nbytes + phi.nbytes),
                "d2h_bytes_per_step": int(phi.nbytes)}
 
+        extras = None if args.no_extras else measure_extras(lq, torch, dev)
+
         cpu = None
         if rank == 0 and size == 1 and not args.no_cpu:
             t_it = oracle_cg_iteration_seconds(U, phi, args.ref_site_fraction)
@@ -312,6 +393,8 @@ def run_ours(args):
             "roofline": roofline, "cg_kernels": cg, "dslash": dsl, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if extras is not None:
+        line["extras"] = extras
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -325,6 +408,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--inner", default="f32_12", choices=["f32", "f32_12", "f16_12", "bf16_12"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extras", action="store_true", help="skip the HMC, batch and iteration-scan numbers")
     ap.add_argument("--ref-site-fraction", type=int, default=8)
     ap.add_argument("--cg-iterations", type=int, default=312,
                     help="FP64 CG iterations of this workload (reference arm extrapolation)")

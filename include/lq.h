@@ -103,6 +103,14 @@ const char* lq_last_error(const lq_ctx* ctx);
 /* Issue subsequent work on another stream (a cudaStream_t). */
 lq_status lq_set_stream(lq_ctx* ctx, void* cuda_stream);
 
+/* Options of a context.
+ *   LQ_OPT_CUDA_GRAPHS  1 (default): CG iterations are recorded once as CUDA graphs and
+ *                       replayed; 0: every kernel is launched from the host (to measure
+ *                       the launch overhead the graphs remove; paper Sec. 4, Fig. 1 reads
+ *                       a per-call overhead off CG time against iteration count). */
+enum { LQ_OPT_CUDA_GRAPHS = 1 };
+lq_status lq_set_option(lq_ctx* ctx, int option, int value);
+
 /* Number of lattice sites V. */
 int64_t lq_volume(const lq_ctx* ctx);
 

@@ -126,6 +126,14 @@ lq_status ensure_solver_fields(lq_ctx* c, int inner) {
 // precision, length and kappa); the kernels return at once after the
 // device-side halt flag is raised.
 lq_status run_chunk(lq_ctx* c, int inner, int n, double kappa) {
+  if (!c->use_graphs) {
+    for (int i = 0; i < n; ++i) {
+      if (inner == LQ_F64) cg64_iteration(c, kappa, c->stream);
+      else cglo_iteration(c, inner, kappa, c->stream);
+    }
+    LQ_CUDA(c, cudaGetLastError());
+    return LQ_OK;
+  }
   auto key = std::make_tuple(0, inner, n, kappa);
   auto it = c->graphs.find(key);
   if (it == c->graphs.end()) {
@@ -443,6 +451,14 @@ lq_status lq_set_stream(lq_ctx* c, void* cuda_stream) {
 }
 
 int64_t lq_volume(const lq_ctx* c) { return c ? (int64_t)c->geo.V : 0; }
+
+lq_status lq_set_option(lq_ctx* c, int option, int value) {
+  if (!c) return LQ_ERR_ARG;
+  switch (option) {
+    case LQ_OPT_CUDA_GRAPHS: c->use_graphs = value ? 1 : 0; return LQ_OK;
+    default: return fail(c, LQ_ERR_ARG, "unknown option");
+  }
+}
 
 lq_status lq_gauge_set(lq_ctx* c, const double* U) {
   if (!c) return LQ_ERR_ARG;

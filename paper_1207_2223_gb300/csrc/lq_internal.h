@@ -91,6 +91,7 @@ struct lq_ctx {
 
   std::map<std::tuple<int, int, int, double>, lq::GraphEntry> graphs;
   void* batch = nullptr;                 // workspace of lq_solve_batch (k_batch.cu)
+  int use_graphs = 1;                    // CG iterations as CUDA graphs (lq_set_option)
 };
 
 namespace lq {

@@ -61,6 +61,7 @@ SIGNATURES = {
     "lq_last_error": (ctypes.c_char_p, [_P]),
     "lq_set_stream": (_I, [_P, _P]),
     "lq_volume": (ctypes.c_int64, [_P]),
+    "lq_set_option": (_I, [_P, _I, _I]),
     "lq_gauge_set": (_I, [_P, _P]),
     "lq_gauge_get": (_I, [_P, _P]),
     "lq_apply_M": (_I, [_P, _P, _P, _D, _I, _I]),
@@ -152,6 +153,13 @@ def lq_last_error(ctx):
 
 def lq_set_stream(ctx, stream):
     _check(ctx, load().lq_set_stream(ctx, stream))
+
+
+LQ_OPT_CUDA_GRAPHS = 1
+
+
+def lq_set_option(ctx, option, value):
+    _check(ctx, load().lq_set_option(ctx, int(option), int(value)))
 
 
 def lq_volume(ctx):
