@@ -39,8 +39,8 @@ SIGMA, SEED, KAPPA, TOL, RELIABLE = 0.25, 2, 0.156, 1e-10, 50
 WORKLOAD = "cg_32x32x32x64"
 
 # Algorithmic (DRAM-minimal) bytes per site, every link and spinor moved once.
-GAUGE_B = {"f64": 576, "f32": 288, "f32_12": 192, "f16_12": 96, "bf16_12": 96}
-SPINOR_B = {"f64": 192, "f32": 96, "f32_12": 96, "f16_12": 52, "bf16_12": 52}   # 16-bit: 48 + 4-byte norm
+GAUGE_B = {"f64": 576, "f32": 288, "f32_12": 192, "f16_12": 96, "bf16_12": 96, "df64": 576}
+SPINOR_B = {"f64": 192, "f32": 96, "f32_12": 96, "f16_12": 52, "bf16_12": 52, "df64": 192}   # 16-bit: 48 + 4-byte norm
 # one application of M: gauge + input spinor + output spinor
 DSLASH_BYTES = {k: GAUGE_B[k] + 2 * SPINOR_B[k] for k in GAUGE_B}
 # the three passes of a CG iteration:
@@ -310,6 +310,17 @@ def run_ours(args):
         value = units / t_job
         launches = int(sum(s["kernel_launches"] for s in stats))
 
+        # the same mixed solve with double-float intermediate reliable updates
+        lq.lq_set_option(ctx, lq.LQ_OPT_DF64_UPDATES, 1)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        solve(inner)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        mixed_df_s = t0.elapsed_time(t1) / 1e3
+        lq.lq_set_option(ctx, lq.LQ_OPT_DF64_UPDATES, 0)
+
         # plain FP64 CG on the same source: the comparison of the metric
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
@@ -323,7 +334,7 @@ def run_ours(args):
         peaks, peak_kind = load_peaks()
         hbm = float(peaks["hbm_gbs"])
         dsl = {}
-        for name in ("f64", "f32", "f32_12", "f16_12", "bf16_12"):
+        for name in ("f64", "df64", "f32", "f32_12", "f16_12", "bf16_12"):
             ms = lq.lq_time_dslash(ctx, phid, KAPPA, False, lq.PRECISIONS[name], 20, False)
             gbs = DSLASH_BYTES[name] * V / (ms * 1e-3) / 1e9
             dsl[name] = {"ms": round(ms, 5), "GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4),
@@ -386,7 +397,8 @@ def run_ours(args):
                        "l2": "working set larger than L2 (gauge %d MB + spinors), no flush"
                              % (DSLASH_BYTES[args.inner] * V // 3 // 2**20),
                        "parallelism": "replicas" if size > 1 else "single"},
-            "time_to_solution_s": {"mixed": mixed_s, "fp64": fp64_s, "speedup": fp64_s / mixed_s},
+            "time_to_solution_s": {"mixed": mixed_s, "fp64": fp64_s, "speedup": fp64_s / mixed_s,
+                                   "mixed_double_float_reliable_updates": mixed_df_s},
             "iterations": {"mixed": stats[-1]["iterations"], "reliable_updates": stats[-1]["reliable_updates"],
                            "fp64": st64["iterations"]},
             "true_rel_resid": {"mixed": stats[-1]["true_rel_resid"], "fp64": st64["true_rel_resid"]},

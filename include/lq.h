@@ -70,8 +70,12 @@ typedef enum {
  *   LQ_F32_12   FP32 links stored as 12 reals (row 3 rebuilt), FP32 spinors
  *   LQ_F16_12   FP16 links (12 reals), FP16 spinors scaled by a per-site FP32 norm,
  *               FP32 arithmetic
- *   LQ_BF16_12  as LQ_F16_12 with BF16 storage */
-typedef enum { LQ_F64 = 0, LQ_F32 = 1, LQ_F32_12 = 2, LQ_F16_12 = 3, LQ_BF16_12 = 4 } lq_prec;
+ *   LQ_BF16_12  as LQ_F16_12 with BF16 storage
+ *   LQ_DF64     links and spinors as double-float pairs (hi + lo FP32, ~48 bits),
+ *               double-float arithmetic on the FP32 pipe: operator applications only
+ *               (lq_apply_M, lq_apply_MdagM, lq_time_dslash); the solver uses it for
+ *               its intermediate reliable updates */
+typedef enum { LQ_F64 = 0, LQ_F32 = 1, LQ_F32_12 = 2, LQ_F16_12 = 3, LQ_BF16_12 = 4, LQ_DF64 = 5 } lq_prec;
 
 typedef struct {
   int iterations;           /* CG iterations (inner iterations for a mixed solve) */
@@ -107,8 +111,13 @@ lq_status lq_set_stream(lq_ctx* ctx, void* cuda_stream);
  *   LQ_OPT_CUDA_GRAPHS  1 (default): CG iterations are recorded once as CUDA graphs and
  *                       replayed; 0: every kernel is launched from the host (to measure
  *                       the launch overhead the graphs remove; paper Sec. 4, Fig. 1 reads
- *                       a per-call overhead off CG time against iteration count). */
-enum { LQ_OPT_CUDA_GRAPHS = 1 };
+ *                       a per-call overhead off CG time against iteration count).
+ *   LQ_OPT_DF64_UPDATES 0 (default): every reliable update of a mixed-precision solve in
+ *                       FP64; 1: the intermediate ones in double-float arithmetic (LQ_DF64)
+ *                       on the FP32 pipe, the final residual certified in FP64.  (On this
+ *                       part the double-float operator is only ~1.3x faster than FP64, so
+ *                       the extra certification pass makes option 1 slower overall.) */
+enum { LQ_OPT_CUDA_GRAPHS = 1, LQ_OPT_DF64_UPDATES = 2 };
 lq_status lq_set_option(lq_ctx* ctx, int option, int value);
 
 /* Number of lattice sites V. */

@@ -73,7 +73,11 @@ lq_status require_gauge(lq_ctx* c, int prec) {
 }
 
 lq_status check_prec(lq_ctx* c, int prec) {
-  if (prec < LQ_F64 || prec > LQ_BF16_12) return fail(c, LQ_ERR_ARG, "unknown precision");
+  if (prec < LQ_F64 || prec > LQ_DF64) return fail(c, LQ_ERR_ARG, "unknown precision");
+  return LQ_OK;
+}
+lq_status check_inner(lq_ctx* c, int prec) {
+  if (prec < LQ_F64 || prec > LQ_BF16_12) return fail(c, LQ_ERR_ARG, "unknown or unsupported solver precision");
   return LQ_OK;
 }
 
@@ -178,8 +182,13 @@ lq_status solve_internal(lq_ctx* c, double kappa, double tol, int maxiter, int i
   LQ_TRY(ensure_solver_fields(c, inner));
   const Geom& g = c->geo;
   const bool mixed = inner != LQ_F64;
+  const bool dfru = mixed && c->df_updates;     // double-float intermediate reliable updates
   SStore slo = spinor_store_of(inner);
   int k = (int)slo;
+  if (dfru) {
+    LQ_TRY(require_gauge(c, LQ_DF64));
+    for (Field* f : {&c->phi_df, &c->x_df, &c->tmp_df, &c->r_df}) LQ_TRY(alloc_field(c, *f, SStore::DF64));
+  }
   SolverState h{};
   h.stop2 = tol * tol;
   h.ru_every = mixed ? reliable_every : 0;
@@ -191,6 +200,10 @@ lq_status solve_internal(lq_ctx* c, double kappa, double tol, int maxiter, int i
   LQ_CUDA(c, cudaMemcpyAsync(c->state, c->state_host, sizeof(SolverState), cudaMemcpyHostToDevice, c->stream));
   if (mixed) {
     launch_zero_spinor(g, SStore::F64, c->x64.ref(), c->stream);
+    if (dfru) {
+      launch_convert_spinor(g, SStore::F64, c->phi64.ref(), SStore::DF64, c->phi_df.ref(), c->stream);
+      launch_zero_spinor(g, SStore::DF64, c->x_df.ref(), c->stream);
+    }
     launch_solver_init(g, c->phi64.ref(), slo, c->x_lo[k].ref(), slo, c->r_lo[k].ref(), slo, c->p_lo[k].ref(),
                        c->state, c->rs, c->stream);
   } else {
@@ -221,15 +234,37 @@ lq_status solve_internal(lq_ctx* c, double kappa, double tol, int maxiter, int i
       const SolverState& st = *c->state_host;
       if (st.breakdown) { result = fail(c, LQ_ERR_NAN, "CG breakdown (non-positive or non-finite curvature)"); break; }
       if (!st.halt) continue;
-      // true residual in FP64; for mixed solves this is the reliable update
-      if (mixed) launch_accumulate_x(g, slo, c->x_lo[k].ref(), c->x64.ref(), c->stream);
-      cg64_true_residual(c, kappa, inner, c->stream);
-      s.kernel_launches += mixed ? 3 : 2;
-      LQ_CUDA(c, cudaGetLastError());
-      LQ_TRY(read_state(c));
+      // true residual; for mixed solves this is the reliable update
+      if (dfru) {
+        // double-float on the FP32 pipe; a residual meeting tol is certified in FP64
+        df_reliable_update(c, kappa, inner, c->stream);
+        s.kernel_launches += 3;
+        LQ_CUDA(c, cudaGetLastError());
+        LQ_TRY(read_state(c));
+        rel = std::sqrt(c->state_host->rr_true / c->state_host->phi2);
+        s.reliable_updates++;
+        if (std::isfinite(rel) && rel <= tol) {
+          launch_convert_spinor(g, SStore::DF64, c->x_df.ref(), SStore::F64, c->x64.ref(), c->stream);
+          cg64_true_residual(c, kappa, inner, c->stream);
+          s.kernel_launches += 3;
+          LQ_CUDA(c, cudaGetLastError());
+          LQ_TRY(read_state(c));
+          rel = std::sqrt(c->state_host->rr_true / c->state_host->phi2);
+          if (std::isfinite(rel) && rel <= tol) { s.converged = 1; break; }
+          // not certified: continue from the FP64 residual
+          launch_convert_spinor(g, SStore::F64, c->r64.ref(), SStore::DF64, c->r_df.ref(), c->stream);
+          s.kernel_launches += 1;
+        }
+      } else {
+        if (mixed) launch_accumulate_x(g, slo, c->x_lo[k].ref(), c->x64.ref(), c->stream);
+        cg64_true_residual(c, kappa, inner, c->stream);
+        s.kernel_launches += mixed ? 3 : 2;
+        LQ_CUDA(c, cudaGetLastError());
+        LQ_TRY(read_state(c));
+        rel = std::sqrt(c->state_host->rr_true / c->state_host->phi2);
+        if (mixed) s.reliable_updates++;
+      }
       const double rr_true = c->state_host->rr_true;
-      rel = std::sqrt(rr_true / c->state_host->phi2);
-      if (mixed) s.reliable_updates++;
       if (!std::isfinite(rel)) { result = fail(c, LQ_ERR_NAN, "non-finite residual"); break; }
       if (rel <= tol) { s.converged = 1; break; }
       if (c->state_host->iter >= maxiter) {
@@ -256,7 +291,12 @@ lq_status solve_internal(lq_ctx* c, double kappa, double tol, int maxiter, int i
         k = (int)slo;
         LQ_TRY(require_gauge(c, inner));
         LQ_TRY(ensure_solver_fields(c, inner));
-        launch_inner_restart(g, c->r64.ref(), slo, c->x_lo[k].ref(), c->r_lo[k].ref(), c->p_lo[k].ref(), c->stream);
+        if (dfru)
+          launch_inner_restart_df(g, c->r_df.ref(), slo, c->x_lo[k].ref(), c->r_lo[k].ref(), c->p_lo[k].ref(),
+                                  c->stream);
+        else
+          launch_inner_restart(g, c->r64.ref(), slo, c->x_lo[k].ref(), c->r_lo[k].ref(), c->p_lo[k].ref(),
+                               c->stream);
         SolverState& hs = *c->state_host;
         hs.rr = hs.rr_prev = hs.rr_ref = rr_true;
         hs.beta = 0.0;
@@ -277,6 +317,11 @@ lq_status solve_internal(lq_ctx* c, double kappa, double tol, int maxiter, int i
       s.kernel_launches += 2;
       LQ_CUDA(c, cudaGetLastError());
     }
+  }
+  if (dfru && !s.converged) {
+    // the current solution lives in the double-float accumulator
+    launch_convert_spinor(g, SStore::DF64, c->x_df.ref(), SStore::F64, c->x64.ref(), c->stream);
+    s.kernel_launches += 1;
   }
   s.iterations = c->state_host->iter;
   s.true_rel_resid = rel;
@@ -422,11 +467,13 @@ lq_status lq_destroy(lq_ctx* c) {
   if (c->stage_in) cudaFree(c->stage_in);
   if (c->stage_out) cudaFree(c->stage_out);
   if (c->stage_gauge) cudaFree(c->stage_gauge);
-  for (Field* f : {&c->phi64, &c->x64, &c->r64, &c->p64, &c->t64, &c->tmp64, &c->y64, &c->chi64}) free_field(*f);
+  for (Field* f : {&c->phi64, &c->x64, &c->r64, &c->p64, &c->t64, &c->tmp64, &c->y64, &c->chi64, &c->phi_df,
+                   &c->x_df, &c->tmp_df, &c->r_df})
+    free_field(*f);
   for (double* d : {c->mom, c->mom0, c->force, c->stage_mom})
     if (d) cudaFree(d);
   if (c->gauge_old) cudaFree(c->gauge_old);
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 5; ++k) {
     free_field(c->r_lo[k]);
     free_field(c->p_lo[k]);
     free_field(c->t_lo[k]);
@@ -456,6 +503,7 @@ lq_status lq_set_option(lq_ctx* c, int option, int value) {
   if (!c) return LQ_ERR_ARG;
   switch (option) {
     case LQ_OPT_CUDA_GRAPHS: c->use_graphs = value ? 1 : 0; return LQ_OK;
+    case LQ_OPT_DF64_UPDATES: c->df_updates = value ? 1 : 0; return LQ_OK;
     default: return fail(c, LQ_ERR_ARG, "unknown option");
   }
 }
@@ -543,7 +591,7 @@ lq_status lq_solve_MdagM(lq_ctx* c, double* x, const double* phi, double kappa, 
                          int inner, int reliable_every, double* hist, int hist_len, lq_solve_stats* stats) {
   const auto t0 = std::chrono::steady_clock::now();
   if (!c) return LQ_ERR_ARG;
-  LQ_TRY(check_prec(c, inner));
+  LQ_TRY(check_inner(c, inner));
   if (!(tol > 0.0) || maxiter <= 0 || reliable_every < 0 || (hist && hist_len < 0))
     return fail(c, LQ_ERR_ARG, "bad tolerance, iteration limit or history length");
   LQ_TRY(require_gauge(c, LQ_F64));
@@ -699,7 +747,7 @@ lq_status lq_pseudofermion_action(lq_ctx* c, const double* phi, double kappa, do
                                   int reliable_every, double* S, double* X) {
   if (!c) return LQ_ERR_ARG;
   if (!S) return fail(c, LQ_ERR_ARG, "null output");
-  LQ_TRY(check_prec(c, inner));
+  LQ_TRY(check_inner(c, inner));
   if (!(tol > 0.0) || maxiter <= 0 || reliable_every < 0)
     return fail(c, LQ_ERR_ARG, "bad tolerance or iteration limit");
   LQ_TRY(require_gauge(c, LQ_F64));
@@ -736,7 +784,7 @@ lq_status lq_hmc_trajectory(lq_ctx* c, const lq_hmc_params* hp, double* p, const
   if (!hp || !out) return fail(c, LQ_ERR_ARG, "null parameters or result");
   if (hp->n_steps <= 0 || !(hp->tau > 0.0) || !(hp->tol > 0.0) || hp->maxiter <= 0 || hp->reliable_every < 0)
     return fail(c, LQ_ERR_ARG, "bad trajectory parameters");
-  LQ_TRY(check_prec(c, hp->inner_prec));
+  LQ_TRY(check_inner(c, hp->inner_prec));
   LQ_TRY(require_gauge(c, LQ_F64));
   LQ_TRY(ensure_md_fields(c));
   LQ_TRY(ensure_solver_fields(c, hp->inner_prec));
@@ -815,7 +863,7 @@ lq_status lq_hmc_trajectory(lq_ctx* c, const lq_hmc_params* hp, double* p, const
 lq_status lq_time_cg_kernel(lq_ctx* c, const double* in, double kappa, int which, int prec, int n, double* ms) {
   if (!c) return LQ_ERR_ARG;
   if (!ms || n <= 0 || which < 0 || which > 3) return fail(c, LQ_ERR_ARG, "need 0 <= which <= 3, n > 0, ms");
-  LQ_TRY(check_prec(c, prec));
+  LQ_TRY(check_inner(c, prec));
   LQ_TRY(require_gauge(c, LQ_F64));
   LQ_TRY(require_gauge(c, prec));
   LQ_TRY(ensure_solver_fields(c, prec));

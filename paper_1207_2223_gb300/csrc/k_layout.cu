@@ -17,14 +17,14 @@ int resident_grid(const void* kernel, int block) {
 
 size_t spinor_bytes(SStore s, int V) {
   switch (s) {
-    case SStore::F64: return (size_t)V * 24 * 8;
+    case SStore::F64: case SStore::DF64: return (size_t)V * 24 * 8;
     case SStore::F32: return (size_t)V * 24 * 4;
     default: return (size_t)V * 24 * 2;
   }
 }
 size_t gauge_bytes(GStore g, int V) {
   switch (g) {
-    case GStore::F64_18: return (size_t)V * 4 * 18 * 8;
+    case GStore::F64_18: case GStore::DF64_18: return (size_t)V * 4 * 18 * 8;
     case GStore::F32_18: return (size_t)V * 4 * 18 * 4;
     case GStore::F32_12: return (size_t)V * 4 * 12 * 4;
     default: return (size_t)V * 4 * 12 * 2;
@@ -59,7 +59,14 @@ __global__ void convert_gauge_kernel(int V, const double2* __restrict__ soa64, v
     double2 u[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) u[c] = soa64[((size_t)mu * 9 + c) * V + s];
-    if constexpr (G == GStore::F32_18) {
+    if constexpr (G == GStore::DF64_18) {
+      float4* o = static_cast<float4*>(out) + (size_t)mu * 9 * V;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const df64 a(u[c].x), b(u[c].y);
+        o[(size_t)c * V + s] = make_float4(a.hi, a.lo, b.hi, b.lo);
+      }
+    } else if constexpr (G == GStore::F32_18) {
       float2* o = static_cast<float2*>(out) + (size_t)mu * 9 * V;
 #pragma unroll
       for (int c = 0; c < 9; ++c) o[(size_t)c * V + s] = make_float2((float)u[c].x, (float)u[c].y);
@@ -121,7 +128,26 @@ void launch_convert_gauge(const Geom& g, const void* soa64, GStore dst, void* ou
     case GStore::F32_12: convert_gauge_kernel<GStore::F32_12><<<grid, kBS, 0, st>>>(g.V, in, out); break;
     case GStore::F16_12: convert_gauge_kernel<GStore::F16_12><<<grid, kBS, 0, st>>>(g.V, in, out); break;
     case GStore::BF16_12: convert_gauge_kernel<GStore::BF16_12><<<grid, kBS, 0, st>>>(g.V, in, out); break;
+    case GStore::DF64_18: convert_gauge_kernel<GStore::DF64_18><<<grid, kBS, 0, st>>>(g.V, in, out); break;
   }
+}
+
+// field-to-field format conversion (through FP64 values)
+template <SStore A, SStore B>
+__global__ void convert_spinor_kernel(int V, SpinorRef in, SpinorRef out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  cplx<double> v[12];
+  load_spinor<A, double>(in, V, s, v);
+  store_spinor<B, double>(out, V, s, v);
+}
+
+void launch_convert_spinor(const Geom& g, SStore a, SpinorRef in, SStore b, SpinorRef out, cudaStream_t st) {
+  const int grid = grid_for(g.V, kBS);
+  if (a == SStore::F64 && b == SStore::DF64)
+    convert_spinor_kernel<SStore::F64, SStore::DF64><<<grid, kBS, 0, st>>>(g.V, in, out);
+  else if (a == SStore::DF64 && b == SStore::F64)
+    convert_spinor_kernel<SStore::DF64, SStore::F64><<<grid, kBS, 0, st>>>(g.V, in, out);
 }
 void launch_pack_spinor(const Geom& g, const double* canon, SStore s, SpinorRef out, cudaStream_t st) {
   const int grid = grid_for(g.V, kBS);
@@ -130,6 +156,7 @@ void launch_pack_spinor(const Geom& g, const double* canon, SStore s, SpinorRef 
     case SStore::F32: pack_spinor_kernel<SStore::F32><<<grid, kBS, 0, st>>>(g.V, canon, out); break;
     case SStore::F16: pack_spinor_kernel<SStore::F16><<<grid, kBS, 0, st>>>(g.V, canon, out); break;
     case SStore::BF16: pack_spinor_kernel<SStore::BF16><<<grid, kBS, 0, st>>>(g.V, canon, out); break;
+    case SStore::DF64: pack_spinor_kernel<SStore::DF64><<<grid, kBS, 0, st>>>(g.V, canon, out); break;
   }
 }
 void launch_unpack_spinor(const Geom& g, SStore s, SpinorRef in, double* canon, cudaStream_t st) {
@@ -139,6 +166,7 @@ void launch_unpack_spinor(const Geom& g, SStore s, SpinorRef in, double* canon, 
     case SStore::F32: unpack_spinor_kernel<SStore::F32><<<grid, kBS, 0, st>>>(g.V, in, canon); break;
     case SStore::F16: unpack_spinor_kernel<SStore::F16><<<grid, kBS, 0, st>>>(g.V, in, canon); break;
     case SStore::BF16: unpack_spinor_kernel<SStore::BF16><<<grid, kBS, 0, st>>>(g.V, in, canon); break;
+    case SStore::DF64: unpack_spinor_kernel<SStore::DF64><<<grid, kBS, 0, st>>>(g.V, in, canon); break;
   }
 }
 

@@ -13,6 +13,8 @@
 //   gauge F32_18 float2  [4][9][V]
 //   gauge F32_12 float4  [4][3][V]        rows 0, 1 only (12 reals)
 //   gauge F16_12 / BF16_12  uint2 [4][3][V]  rows 0, 1 only, 4 reals per chunk
+//   spinor DF64  float4 [12][V]           (re.hi, re.lo, im.hi, im.lo) double-float
+//   gauge DF64_18 float4 [4][9][V]        double-float, 18 reals
 // Links stored with 12 reals are rebuilt on the fly with
 // row 2 = conj(row 0 x row 1), exact for SU(3).  The antiperiodic time
 // boundary is applied as a sign on the hop, never folded into links, so
@@ -23,6 +25,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <type_traits>
+
+#include "lq_df64.cuh"
 
 namespace lq {
 
@@ -57,8 +61,14 @@ template <typename T> __device__ __forceinline__ cplx<T> conjg(cplx<T> a) { retu
 template <typename T> __device__ __forceinline__ T norm2(cplx<T> a) { return a.re * a.re + a.im * a.im; }
 
 // ---------------------------------------------------------------- formats
-enum class SStore : int { F64 = 0, F32 = 1, F16 = 2, BF16 = 3 };
-enum class GStore : int { F64_18 = 0, F32_18 = 1, F32_12 = 2, F16_12 = 3, BF16_12 = 4 };
+enum class SStore : int { F64 = 0, F32 = 1, F16 = 2, BF16 = 3, DF64 = 4 };
+enum class GStore : int { F64_18 = 0, F32_18 = 1, F32_12 = 2, F16_12 = 3, BF16_12 = 4, DF64_18 = 5 };
+
+// Conversions of a double-float to the arithmetic type of a kernel.
+template <typename T> __device__ __forceinline__ T from_df(df64 v) { return (T)v; }
+template <> __device__ __forceinline__ df64 from_df<df64>(df64 v) { return v; }
+template <typename T> __device__ __forceinline__ df64 to_df(T v) { return df64(v); }
+template <> __device__ __forceinline__ df64 to_df<df64>(df64 v) { return v; }
 
 struct SpinorRef {           // device view of one spinor field
   void* p;                   // chunk array
@@ -98,6 +108,7 @@ template <> struct SpinorTraits<SStore::F64> { using half_t = void; };
 template <> struct SpinorTraits<SStore::F32> { using half_t = void; };
 template <> struct SpinorTraits<SStore::F16> { using half_t = __half; };
 template <> struct SpinorTraits<SStore::BF16> { using half_t = __nv_bfloat16; };
+template <> struct SpinorTraits<SStore::DF64> { using half_t = void; };
 
 // ----------------------------------------------------------- spinor I/O
 // RO = true: the field is read-only for the whole kernel, so loads may use
@@ -108,7 +119,14 @@ template <bool RO, typename W> __device__ __forceinline__ W ld(const W* p) {
 
 template <SStore S, typename T, bool RO = true>
 __device__ __forceinline__ void load_spinor(const SpinorRef& f, int V, int s, cplx<T> v[12]) {
-  if constexpr (S == SStore::F64) {
+  if constexpr (S == SStore::DF64) {
+    const float4* p = static_cast<const float4*>(f.p);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      float4 w = ld<RO>(p + (size_t)c * V + s);
+      v[c] = {from_df<T>(df64(w.x, w.y)), from_df<T>(df64(w.z, w.w))};
+    }
+  } else if constexpr (S == SStore::F64) {
     const double2* p = static_cast<const double2*>(f.p);
 #pragma unroll
     for (int c = 0; c < 12; ++c) { double2 w = ld<RO>(p + (size_t)c * V + s); v[c] = {(T)w.x, (T)w.y}; }
@@ -140,7 +158,7 @@ __device__ __forceinline__ void load_spinor(const SpinorRef& f, int V, int s, cp
 // spinor, half as many multiplications as scaling all 24 reals.
 template <SStore S, typename T>
 __device__ __forceinline__ T load_spinor_raw(const SpinorRef& f, int V, int s, cplx<T> v[12]) {
-  if constexpr (S == SStore::F64 || S == SStore::F32) {
+  if constexpr (S == SStore::F64 || S == SStore::F32 || S == SStore::DF64) {
     load_spinor<S, T>(f, V, s, v);
     return (T)1;
   } else {
@@ -162,7 +180,14 @@ __device__ __forceinline__ T load_spinor_raw(const SpinorRef& f, int V, int s, c
 
 template <SStore S, typename T>
 __device__ __forceinline__ void store_spinor(const SpinorRef& f, int V, int s, const cplx<T> v[12]) {
-  if constexpr (S == SStore::F64) {
+  if constexpr (S == SStore::DF64) {
+    float4* p = static_cast<float4*>(f.p);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      const df64 a = to_df<T>(v[c].re), b = to_df<T>(v[c].im);
+      p[(size_t)c * V + s] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+  } else if constexpr (S == SStore::F64) {
     double2* p = static_cast<double2*>(f.p);
 #pragma unroll
     for (int c = 0; c < 12; ++c) p[(size_t)c * V + s] = make_double2((double)v[c].re, (double)v[c].im);
@@ -198,6 +223,7 @@ template <> struct GaugeTraits<GStore::F32_18> { using half_t = void; };
 template <> struct GaugeTraits<GStore::F32_12> { using half_t = void; };
 template <> struct GaugeTraits<GStore::F16_12> { using half_t = __half; };
 template <> struct GaugeTraits<GStore::BF16_12> { using half_t = __nv_bfloat16; };
+template <> struct GaugeTraits<GStore::DF64_18> { using half_t = void; };
 
 template <typename T>
 __device__ __forceinline__ void reconstruct_row2(cplx<T> u[9]) {
@@ -208,7 +234,14 @@ __device__ __forceinline__ void reconstruct_row2(cplx<T> u[9]) {
 
 template <GStore G, typename T>
 __device__ __forceinline__ void load_link(const GaugeRef& g, int V, int mu, int s, cplx<T> u[9]) {
-  if constexpr (G == GStore::F64_18) {
+  if constexpr (G == GStore::DF64_18) {
+    const float4* p = static_cast<const float4*>(g.p) + (size_t)mu * 9 * V;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      float4 w = __ldg(p + (size_t)c * V + s);
+      u[c] = {from_df<T>(df64(w.x, w.y)), from_df<T>(df64(w.z, w.w))};
+    }
+  } else if constexpr (G == GStore::F64_18) {
     const double2* p = static_cast<const double2*>(g.p) + (size_t)mu * 9 * V;
 #pragma unroll
     for (int c = 0; c < 9; ++c) { double2 w = __ldg(p + (size_t)c * V + s); u[c] = {(T)w.x, (T)w.y}; }

@@ -107,6 +107,7 @@ __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, cons
 // registers per thread would otherwise leave one block per SM.
 template <typename T> struct DslashBlock { static constexpr int value = 256; };
 template <> struct DslashBlock<double> { static constexpr int value = 128; };
+template <> struct DslashBlock<df64> { static constexpr int value = 128; };
 // Minimum resident blocks per SM requested from the compiler (register cap).
 #ifndef LQ_DSLASH_MIN_BLOCKS
 #define LQ_DSLASH_MIN_BLOCKS 2

@@ -13,7 +13,7 @@
 
 namespace lq {
 
-constexpr int kNumPrec = 5;   // LQ_F64 .. LQ_BF16_12
+constexpr int kNumPrec = 6;   // LQ_F64 .. LQ_DF64
 
 inline GStore gauge_store_of(int prec) {
   switch (prec) {
@@ -21,6 +21,7 @@ inline GStore gauge_store_of(int prec) {
     case LQ_F32: return GStore::F32_18;
     case LQ_F32_12: return GStore::F32_12;
     case LQ_F16_12: return GStore::F16_12;
+    case LQ_DF64: return GStore::DF64_18;
     default: return GStore::BF16_12;
   }
 }
@@ -29,6 +30,7 @@ inline SStore spinor_store_of(int prec) {
     case LQ_F64: return SStore::F64;
     case LQ_F32: case LQ_F32_12: return SStore::F32;
     case LQ_F16_12: return SStore::F16;
+    case LQ_DF64: return SStore::DF64;
     default: return SStore::BF16;
   }
 }
@@ -58,8 +60,8 @@ struct lq_ctx {
 
   // gauge field: FP64 master copy and lazily built low-precision copies
   void* gauge64 = nullptr;
-  void* gauge_lo[lq::kNumPrec] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  bool gauge_lo_valid[lq::kNumPrec] = {false, false, false, false, false};
+  void* gauge_lo[lq::kNumPrec] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool gauge_lo_valid[lq::kNumPrec] = {false, false, false, false, false, false};
   bool gauge_set = false;
 
   // canonical-layout staging buffers (device)
@@ -69,8 +71,10 @@ struct lq_ctx {
 
   // FP64 solver fields
   lq::Field phi64, x64, r64, p64, t64, tmp64;
-  // low-precision solver fields, one set per storage format
-  lq::Field r_lo[4], p_lo[4], t_lo[4], x_lo[4];
+  // low-precision solver fields, one set per storage format (indexed by SStore)
+  lq::Field r_lo[5], p_lo[5], t_lo[5], x_lo[5];
+  // double-float reliable updates: phi, the accumulated solution, M x, the residual
+  lq::Field phi_df, x_df, tmp_df, r_df;
 
   // molecular dynamics: momenta / forces double [32][V], the start momenta,
   // the force buffer, the gauge field at the start of a trajectory, Y = M X
@@ -92,6 +96,7 @@ struct lq_ctx {
   std::map<std::tuple<int, int, int, double>, lq::GraphEntry> graphs;
   void* batch = nullptr;                 // workspace of lq_solve_batch (k_batch.cu)
   int use_graphs = 1;                    // CG iterations as CUDA graphs (lq_set_option)
+  int df_updates = 0;                    // double-float intermediate reliable updates (lq_set_option)
 };
 
 namespace lq {
@@ -105,6 +110,8 @@ void launch_unpack_gauge64(const Geom& g, const void* soa, double* canon, cudaSt
 void launch_convert_gauge(const Geom& g, const void* soa64, GStore dst, void* out, cudaStream_t st);
 void launch_pack_spinor(const Geom& g, const double* canon, SStore s, SpinorRef out, cudaStream_t st);
 void launch_unpack_spinor(const Geom& g, SStore s, SpinorRef in, double* canon, cudaStream_t st);
+// FP64 <-> double-float field conversion
+void launch_convert_spinor(const Geom& g, SStore a, SpinorRef in, SStore b, SpinorRef out, cudaStream_t st);
 
 // ---- BLAS-1 (k_blas.cu)
 // phi2 = |phi|^2 -> state; x = 0; r = phi; p = phi (each in its own format)
@@ -129,6 +136,13 @@ void apply_M_prec(const Geom& g, int prec, const void* gauge, SpinorRef in, Spin
 // ---- FP64 CG pieces (k_cg64.cu)
 void cg64_iteration(lq_ctx* c, double kappa, cudaStream_t stream);
 void cg64_true_residual(lq_ctx* c, double kappa, int store_lo_prec, cudaStream_t stream);
+
+// ---- double-float reliable update (k_cgdf.cu): x_df += x_lo; r = phi_df - M^dag M x_df
+// stored as r_df and in the inner format r_lo[prec]; |r|^2 -> state->rr_true
+void df_reliable_update(lq_ctx* c, double kappa, int inner_prec, cudaStream_t stream);
+// x = 0, r = p = src in format s, from a double-float residual
+void launch_inner_restart_df(const Geom& g, SpinorRef src, SStore s, SpinorRef x, SpinorRef r, SpinorRef p,
+                             cudaStream_t stream);
 
 // ---- low-precision CG iteration (k_cglo.cu)
 void cglo_iteration(lq_ctx* c, int prec, double kappa, cudaStream_t stream);

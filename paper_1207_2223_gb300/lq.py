@@ -14,8 +14,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblq.so")
 
 LQ_OK, LQ_ERR_ARG, LQ_ERR_SHAPE, LQ_ERR_CUDA, LQ_ERR_NOT_CONVERGED, LQ_ERR_NAN, LQ_ERR_STATE = range(7)
-LQ_F64, LQ_F32, LQ_F32_12, LQ_F16_12, LQ_BF16_12 = range(5)
-PRECISIONS = {"f64": LQ_F64, "f32": LQ_F32, "f32_12": LQ_F32_12, "f16_12": LQ_F16_12, "bf16_12": LQ_BF16_12}
+LQ_F64, LQ_F32, LQ_F32_12, LQ_F16_12, LQ_BF16_12, LQ_DF64 = range(6)
+PRECISIONS = {"f64": LQ_F64, "f32": LQ_F32, "f32_12": LQ_F32_12, "f16_12": LQ_F16_12, "bf16_12": LQ_BF16_12,
+              "df64": LQ_DF64}
 
 
 class LQError(RuntimeError):
@@ -155,7 +156,7 @@ def lq_set_stream(ctx, stream):
     _check(ctx, load().lq_set_stream(ctx, stream))
 
 
-LQ_OPT_CUDA_GRAPHS = 1
+LQ_OPT_CUDA_GRAPHS, LQ_OPT_DF64_UPDATES = 1, 2
 
 
 def lq_set_option(ctx, option, value):

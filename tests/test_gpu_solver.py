@@ -54,6 +54,29 @@ def test_solve_matches_oracle(lq, dims, kappa, sigma, prec):
         assert abs(n - it_ref10) <= max(3, it_ref10 // 20), (n, it_ref10)
 
 
+@pytest.mark.parametrize("df_updates", [0, 1])
+def test_mixed_solve_with_and_without_double_float_updates(lq, df_updates):
+    """Reliable updates in FP64 or in double-float (certified in FP64 at the end): same
+    iteration count on a well-conditioned system, both to a 1e-10 FP64 residual."""
+    dims = (6, 4, 4, 8)
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, 0.3, 5)
+    phi = source(lat, 5)
+    x_ref, _, _ = cg_MdagM(U, phi, dims, 0.15, tol=1e-13)
+    ctx = lq.lq_create(dims)
+    try:
+        lq.lq_set_option(ctx, lq.LQ_OPT_DF64_UPDATES, df_updates)
+        lq.lq_gauge_set(ctx, dev(U))
+        x = torch.zeros_like(dev(phi))
+        status, st = lq.lq_solve_MdagM(ctx, x, dev(phi), 0.15, 1e-10, 5000, lq.LQ_F32_12, 20)
+        got = host(x)
+    finally:
+        lq.lq_destroy(ctx)
+    assert status == lq.LQ_OK and st["true_rel_resid"] <= 1e-10
+    assert rel_err(got, x_ref) < X_TOL
+    assert st["reliable_updates"] >= 2
+
+
 def test_zero_source_and_errors(lq):
     dims = (4, 4, 4, 4)
     lat = Lattice(dims)
@@ -78,6 +101,8 @@ def test_zero_source_and_errors(lq):
         assert e.value.status == lq.LQ_ERR_NAN
         with pytest.raises(lq.LQError):
             lq.lq_solve_MdagM(ctx, x, phi, 0.15, -1.0)
+        with pytest.raises(lq.LQError):
+            lq.lq_solve_MdagM(ctx, x, phi, 0.15, 1e-10, 100, lq.LQ_DF64)   # operator-only precision
     finally:
         lq.lq_destroy(ctx)
 
