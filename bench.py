@@ -186,6 +186,23 @@ def measure_extras(lq, torch, dev):
         lq.lq_destroy(ctx)
     out["batch_24x24x24x24_12rhs"] = {"seconds": tb, "sequential_seconds": ts, "iterations": st["iterations"],
                                       "max_true_rel_resid": float(resid.max())}
+    # register ablation (paper Sec. 3-4): naive global-memory FP64 operator against the
+    # optimised FP64 and FP32-12 ones, 32^3 x 64
+    lat = Lattice(DIMS)
+    U = torch.from_numpy(gauge_exp_iA(lat, SIGMA, SEED)).to(dev)
+    phi = torch.from_numpy(source(lat, SEED)).to(dev)
+    ctx = lq.lq_create(DIMS, True, torch.cuda.current_stream(dev).cuda_stream)
+    try:
+        lq.lq_gauge_set(ctx, U)
+        out_t = torch.empty_like(phi)
+        naive = lq.lq_apply_M_naive(ctx, out_t, phi, KAPPA, False, 3)
+        opt64 = lq.lq_time_dslash(ctx, phi, KAPPA, False, lq.LQ_F64, 10, False)
+        opt32 = lq.lq_time_dslash(ctx, phi, KAPPA, False, lq.LQ_F32_12, 20, False)
+    finally:
+        lq.lq_destroy(ctx)
+    out["register_ablation_32x32x32x64"] = {"naive_f64_ms": naive, "optimised_f64_ms": opt64,
+                                            "optimised_f32_12_ms": opt32, "f64_speedup": naive / opt64,
+                                            "f32_12_speedup": naive / opt32}
     # CG time against iteration count, FP64 CG stopped by the iteration limit (tol 1e-30),
     # with and without CUDA graphs; 8^4 (launch-bound) and 16^4
     for dims in ((8, 8, 8, 8), (16, 16, 16, 16)):

@@ -311,6 +311,15 @@ lq_status lq_apply_MdagM_static(double* out, const double* U, const double* in, 
  * overwritten.  The iteration is the paper's CG routine (Sec. 3).  Synchronises. */
 lq_status lq_time_cg_kernel(lq_ctx* ctx, const double* in, double kappa, int which, int prec, int n, double* ms);
 
+/* Ablation of the paper's register observation (Sec. 3 and 4: the array variables of
+ * the kernels moved from global memory into registers, a fivefold speed-up on Fermi).
+ * out = M in (dagger 0) or M^dag in (1), FP64, computed by a naive kernel: canonical
+ * array-of-structures layout, a neighbour table in global memory, dense 4x4 spin
+ * matrices and accumulation through global memory.  in, out: device, canonical.
+ * When n > 0 and ms != NULL, the kernel is then launched n more times and *ms receives
+ * its average device time (CUDA events on the context's stream).  Synchronises. */
+lq_status lq_apply_M_naive(lq_ctx* ctx, double* out, const double* in, double kappa, int dagger, int n, double* ms);
+
 #ifdef __cplusplus
 }
 #endif

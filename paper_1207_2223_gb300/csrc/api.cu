@@ -860,6 +860,44 @@ lq_status lq_hmc_trajectory(lq_ctx* c, const lq_hmc_params* hp, double* p, const
   return LQ_OK;
 }
 
+lq_status lq_apply_M_naive(lq_ctx* c, double* out, const double* in, double kappa, int dagger, int n, double* ms) {
+  if (!c) return LQ_ERR_ARG;
+  if (!out || !in || in == out || n < 0) return fail(c, LQ_ERR_ARG, "bad buffers or count");
+  if (!is_device_ptr(out) || !is_device_ptr(in) || !aligned16(out) || !aligned16(in))
+    return fail(c, LQ_ERR_ARG, "naive operator: device buffers, 16-byte aligned");
+  LQ_TRY(require_gauge(c, LQ_F64));
+  const size_t V = c->geo.V;
+  int* nbr = nullptr;
+  double* sgn = nullptr;
+  double* Ucanon = nullptr;
+  LQ_CUDA(c, cudaMallocAsync((void**)&nbr, sizeof(int) * 8 * V, c->stream));
+  LQ_CUDA(c, cudaMallocAsync((void**)&sgn, sizeof(double) * 8 * V, c->stream));
+  LQ_CUDA(c, cudaMallocAsync((void**)&Ucanon, sizeof(double) * 72 * V, c->stream));
+  naive_setup(c, &nbr, &sgn);
+  launch_unpack_gauge64(c->geo, c->gauge64, Ucanon, c->stream);
+  launch_naive_dslash(c, nbr, sgn, Ucanon, in, out, kappa, dagger);
+  lq_status st = cuda_check(c, cudaGetLastError(), "naive operator");
+  if (st == LQ_OK && n > 0 && ms) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, c->stream);
+    for (int i = 0; i < n; ++i) launch_naive_dslash(c, nbr, sgn, Ucanon, in, out, kappa, dagger);
+    cudaEventRecord(e1, c->stream);
+    st = cuda_check(c, cudaEventSynchronize(e1), "cudaEventSynchronize");
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    *ms = t / n;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  cudaFreeAsync(nbr, c->stream);
+  cudaFreeAsync(sgn, c->stream);
+  cudaFreeAsync(Ucanon, c->stream);
+  lq_status fin = cuda_check(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  return st == LQ_OK ? fin : st;
+}
+
 lq_status lq_time_cg_kernel(lq_ctx* c, const double* in, double kappa, int which, int prec, int n, double* ms) {
   if (!c) return LQ_ERR_ARG;
   if (!ms || n <= 0 || which < 0 || which > 3) return fail(c, LQ_ERR_ARG, "need 0 <= which <= 3, n > 0, ms");

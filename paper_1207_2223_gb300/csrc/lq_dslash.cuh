@@ -113,6 +113,13 @@ template <> struct DslashBlock<df64> { static constexpr int value = 128; };
 #define LQ_DSLASH_MIN_BLOCKS 2
 #endif
 
+// Pass 1 of CG and the plain operator (no epilogue loads) are latency-bound:
+// they may ask for more resident blocks than pass 2.
+#ifndef LQ_K1_MIN_BLOCKS
+#define LQ_K1_MIN_BLOCKS LQ_DSLASH_MIN_BLOCKS
+#endif
+template <typename T, class Epi> struct EpiMinBlocks { static constexpr int value = LQ_DSLASH_MIN_BLOCKS; };
+
 // |v|^2 of one site in the kernel's arithmetic precision; the per-site sums
 // are then accumulated in FP64 (one FP64 add per site: the FP64 pipe of this
 // part is ~60x slower than its FP32 pipe).
@@ -128,7 +135,7 @@ __device__ __forceinline__ double site_norm2(const cplx<T> v[12]) {
 // walks the lattice in steps of the grid size, so the halt check and the
 // block reduction happen once per block rather than once per 256 sites.
 template <typename T, GStore G, SStore SI, bool DAG, class Epi>
-__global__ void __launch_bounds__(DslashBlock<T>::value, LQ_DSLASH_MIN_BLOCKS) dslash_kernel(Geom geo, GaugeRef U, SpinorRef in,
+__global__ void __launch_bounds__(DslashBlock<T>::value, (EpiMinBlocks<T, Epi>::value)) dslash_kernel(Geom geo, GaugeRef U, SpinorRef in,
                                                                         T kappa, Epi epi, ReduceScratch rs) {
   if (epi.halted()) return;
   double red[Epi::NRED];
@@ -255,6 +262,9 @@ struct EpiCG2 {
     if (st->iter >= st->maxiter) st->halt = 1;
   }
 };
+
+template <SStore S> struct EpiMinBlocks<float, EpiCG1<S>> { static constexpr int value = LQ_K1_MIN_BLOCKS; };
+template <SStore S> struct EpiMinBlocks<float, EpiStore<S>> { static constexpr int value = LQ_K1_MIN_BLOCKS; };
 
 // True residual in FP64:  v = M^dag (M x)  ->  r = phi - v, |r|^2.
 // Optionally also stores r in a low-precision field (reliable update).

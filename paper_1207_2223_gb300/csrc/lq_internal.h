@@ -101,6 +101,11 @@ struct lq_ctx {
 
 namespace lq {
 
+// ---- naive operator for the register ablation (k_naive.cu)
+void naive_setup(lq_ctx* c, int** nbr, double** sgn);
+void launch_naive_dslash(lq_ctx* c, const int* nbr, const double* sgn, const double* Ucanon, const double* in,
+                         double* out, double kappa, int dagger);
+
 // ---- batched solves (k_batch.cu)
 void destroy_batch_work(void* w);
 

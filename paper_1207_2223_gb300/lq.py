@@ -73,6 +73,7 @@ SIGNATURES = {
     "lq_time_cg_kernel": (_I, [_P, _P, _D, _I, _I, _I, ctypes.POINTER(_D)]),
     "lq_solve_batch": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_D), _I,
                             _D, _I, _I, _I, _P, _I, _P, _P, ctypes.POINTER(lq_solve_stats)]),
+    "lq_apply_M_naive": (_I, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(_D)]),
     "lq_plaquette": (_I, [_P, ctypes.POINTER(_D)]),
     "lq_gauge_action": (_I, [_P, _D, ctypes.POINTER(_D)]),
     "lq_gauge_force": (_I, [_P, _P, _D]),
@@ -230,6 +231,14 @@ def lq_solve_batch(ctxs, xs, phis, kappas, nrhs=1, tol=1e-10, maxiter=100000, in
     if status not in (LQ_OK, LQ_ERR_NOT_CONVERGED):
         _check(ctxs[0], status)
     return status, st.as_dict(), iters, resid, hist
+
+
+def lq_apply_M_naive(ctx, out, inp, kappa, dagger=False, n=0):
+    """Naive-kernel M (ablation); with n > 0 returns its average device ms over n launches."""
+    ms = _D(0.0)
+    _check(ctx, load().lq_apply_M_naive(ctx, _ptr(out), _ptr(inp), float(kappa), 1 if dagger else 0, int(n),
+                                        ctypes.byref(ms)))
+    return ms.value
 
 
 def lq_plaquette(ctx):
