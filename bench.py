@@ -272,6 +272,17 @@ def run_kernel_only(args):
     lq.lq_gauge_set(ctx, torch.from_numpy(U).cuda())
     p = torch.from_numpy(phi).cuda()
     prec = lq.PRECISIONS[args.prec]
+    if args.kernel_only == "batch":
+        import numpy as np
+        R = 12
+        phis = torch.from_numpy(np.stack([source(lat, SEED, i) for i in range(R)])).cuda()
+        x = torch.zeros_like(phis)
+        t0 = time.perf_counter()
+        st = lq.lq_solve_batch([ctx], [x], [phis], [KAPPA], R, 1e-10, args.steps, prec, 50)
+        lq.lq_destroy(ctx)
+        print("batch %s %s x %d: %d iterations, %.4f s" % (args.prec, dims, R, st[1]["iterations"],
+                                                          time.perf_counter() - t0))
+        return 0
     if args.kernel_only == "dslash":
         ms = lq.lq_time_dslash(ctx, p, KAPPA, False, prec, args.steps, False)
     else:
@@ -441,8 +452,9 @@ def main():
     ap.add_argument("--ref-site-fraction", type=int, default=8)
     ap.add_argument("--cg-iterations", type=int, default=312,
                     help="FP64 CG iterations of this workload (reference arm extrapolation)")
-    ap.add_argument("--kernel-only", default=None, choices=["dslash", "k1", "k2", "k3"],
-                    help="profiling target: only launch this kernel (precision --prec)")
+    ap.add_argument("--kernel-only", default=None, choices=["dslash", "k1", "k2", "k3", "batch"],
+                    help="profiling target: only launch this kernel (precision --prec); batch: a 12-RHS "
+                         "batched solve of --steps iterations")
     ap.add_argument("--prec", default="f32_12", choices=["f64", "f32", "f32_12", "f16_12", "bf16_12"])
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
     args = ap.parse_args()

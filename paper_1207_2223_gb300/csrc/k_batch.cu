@@ -247,8 +247,20 @@ __global__ void __launch_bounds__(256) batch_dslash_kernel(BatchDesc bd, SpinorR
   double* sh_col = smem + blockDim.x;     // [ncols]
   for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) sh_col[c] = 0.0;
   __syncthreads();
+  // A thread's column is fixed while the block stays inside one system (the
+  // tile is a multiple of R), so it sums in a register and the block folds
+  // the sums into sh_col only when the system changes (block-uniform).
+  int cur = -1;
+  double acc_v = 0.0;
   for (int t = blockIdx.x; t < bd.ntiles; t += gridDim.x) {
     const int k = system_of_tile(bd, t);
+    if constexpr (Epi::REDUCE) {
+      if (k != cur) {
+        if (cur >= 0) tile_columns(bd.sys[cur], acc_v, sh_tile, sh_col);
+        cur = k;
+        acc_v = 0.0;
+      }
+    }
     const SysDesc& sd = bd.sys[k];
     const int e_loc = (t - sd.tile0) * bd.tile + threadIdx.x;
     double v = 0.0;
@@ -275,9 +287,10 @@ __global__ void __launch_bounds__(256) batch_dslash_kernel(BatchDesc bd, SpinorR
       }
       v = epi.apply(ix(s), sd.col + r, acc);
     }
-    if constexpr (Epi::REDUCE) tile_columns(sd, v, sh_tile, sh_col);
+    acc_v += v;
   }
   if constexpr (Epi::REDUCE) {
+    if (cur >= 0) tile_columns(bd.sys[cur], acc_v, sh_tile, sh_col);
     auto fin = [&](const double* tot) { epi.finalize_cols(tot, bd.ncols); };
     batch_grid_sum(bd, sh_col, br, fin);
   }
@@ -449,10 +462,13 @@ BatchDesc make_desc(lq_ctx** ctxs, int n, int R, const double* const* phi, doubl
   return bd;
 }
 
+// One wave of resident blocks: a second wave would sweep the lattice again
+// after the first, losing the L2 reuse of neighbour spinors.
 template <typename T, GStore G, SStore SI, bool DAG, class Epi>
 void launch_batch(const BatchDesc& bd, SpinorRef in, const Epi& epi, const BatchReduce& br, int use64,
                   int grid_cap, cudaStream_t st) {
-  const int grid = std::min(bd.ntiles, grid_cap);
+  const int wave = resident_grid(reinterpret_cast<const void*>(&batch_dslash_kernel<T, G, SI, DAG, Epi>), bd.tile);
+  const int grid = std::min(std::min(bd.ntiles, grid_cap), wave);
   const size_t sh = sizeof(double) * (bd.tile + bd.ncols);
   batch_dslash_kernel<T, G, SI, DAG, Epi><<<grid, bd.tile, sh, st>>>(bd, in, epi, br, use64);
 }
@@ -611,6 +627,8 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
     cudaMemcpyAsync(w->st, w->st_host, sizeof(BatchState), cudaMemcpyHostToDevice, st);
   }
   const BatchDesc bd = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, w->tile);
+  // FP64 passes (~140 registers per thread) use tiles of about 128 threads
+  const BatchDesc bd64 = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, std::max(nrhs, 128 / nrhs * nrhs));
   const int grid = std::min(bd.ntiles, w->grid_cap);
   batch_init_kernel<<<grid, bd.tile, sizeof(double) * (bd.tile + bd.ncols), st>>>(
       bd, w->phi64.ref(), w->x64.ref(), w->xlo.ref(), w->rlo.ref(), w->plo.ref(), w->st, w->br);
@@ -647,7 +665,7 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
     s.kernel_launches += 3 * chunk;
     // reliable update: fold x, FP64 true residual per column, freeze converged columns
     batch_accumulate_kernel<<<grid, bd.tile, 0, st>>>(bd.total, w->xlo.ref(), w->x64.ref());
-    batch_true_residual(w, bd, st);
+    batch_true_residual(w, bd64, st);
     batch_xpay_kernel<<<grid, bd.tile, 0, st>>>(bd, w->rlo.ref(), w->plo.ref(), w->st, 1);
     s.kernel_launches += 4;
     s.reliable_updates++;
