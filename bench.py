@@ -6,8 +6,9 @@ U = exp(iA), A traceless Hermitian with N(0, 0.25^2) entries (seed 2),
 kappa = 0.156, antiperiodic time, a complex Gaussian source; M^dag M x = phi
 is solved from x0 = 0 to an FP64 true relative residual of 1e-10.
 
-One step = one mixed-precision solve (inner precision --inner, FP64
-reliable updates every 50 iterations).  Printed as one JSON line:
+One step = one mixed-precision solve (inner precision --inner, default
+16-bit fixed-point storage with 12-real links and per-site norms, FP32
+arithmetic, FP64 reliable updates every 50 iterations).  Printed as one JSON line:
   value         solves per second over all ranks (device-timed, data resident)
   e2e           the same through the C interface with pinned host buffers
                 (gauge field and source copied in, solution copied out, every step)
@@ -39,8 +40,9 @@ SIGMA, SEED, KAPPA, TOL, RELIABLE = 0.25, 2, 0.156, 1e-10, 50
 WORKLOAD = "cg_32x32x32x64"
 
 # Algorithmic (DRAM-minimal) bytes per site, every link and spinor moved once.
-GAUGE_B = {"f64": 576, "f32": 288, "f32_12": 192, "f16_12": 96, "bf16_12": 96, "df64": 576}
-SPINOR_B = {"f64": 192, "f32": 96, "f32_12": 96, "f16_12": 52, "bf16_12": 52, "df64": 192}   # 16-bit: 48 + 4-byte norm
+GAUGE_B = {"f64": 576, "f32": 288, "f32_12": 192, "f16_12": 96, "bf16_12": 96, "df64": 576, "i16_12": 96}
+SPINOR_B = {"f64": 192, "f32": 96, "f32_12": 96, "f16_12": 52, "bf16_12": 52, "df64": 192,
+            "i16_12": 52}   # 16-bit: 48 + 4-byte norm
 # one application of M: gauge + input spinor + output spinor
 DSLASH_BYTES = {k: GAUGE_B[k] + 2 * SPINOR_B[k] for k in GAUGE_B}
 # the three passes of a CG iteration:
@@ -338,6 +340,21 @@ def run_ours(args):
         value = units / t_job
         launches = int(sum(s["kernel_launches"] for s in stats))
 
+        # the other inner storage formats, one solve each (FP16-12 is the storage the
+        # 32^3 x 64 workload names; FP32-12 is HBM-bound, the 16-bit formats issue-bound)
+        others = {}
+        for name in ("f32_12", "f16_12", "bf16_12", "i16_12"):
+            if name == args.inner:
+                continue
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            sto = solve(lq.PRECISIONS[name])
+            q1.record(stream)
+            torch.cuda.synchronize(dev)
+            others[name] = {"seconds": q0.elapsed_time(q1) / 1e3, "iterations": sto["iterations"],
+                            "reliable_updates": sto["reliable_updates"], "escalations": sto["escalations"]}
+
         # the same mixed solve with double-float intermediate reliable updates
         lq.lq_set_option(ctx, lq.LQ_OPT_DF64_UPDATES, 1)
         t0 = torch.cuda.Event(enable_timing=True)
@@ -362,7 +379,7 @@ def run_ours(args):
         peaks, peak_kind = load_peaks()
         hbm = float(peaks["hbm_gbs"])
         dsl = {}
-        for name in ("f64", "df64", "f32", "f32_12", "f16_12", "bf16_12"):
+        for name in ("f64", "df64", "f32", "f32_12", "f16_12", "bf16_12", "i16_12"):
             ms = lq.lq_time_dslash(ctx, phid, KAPPA, False, lq.PRECISIONS[name], 20, False)
             gbs = DSLASH_BYTES[name] * V / (ms * 1e-3) / 1e9
             dsl[name] = {"ms": round(ms, 5), "GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4),
@@ -426,7 +443,8 @@ def run_ours(args):
                              % (DSLASH_BYTES[args.inner] * V // 3 // 2**20),
                        "parallelism": "replicas" if size > 1 else "single"},
             "time_to_solution_s": {"mixed": mixed_s, "fp64": fp64_s, "speedup": fp64_s / mixed_s,
-                                   "mixed_double_float_reliable_updates": mixed_df_s},
+                                   "mixed_double_float_reliable_updates": mixed_df_s,
+                                   "other_inner_formats": others},
             "iterations": {"mixed": stats[-1]["iterations"], "reliable_updates": stats[-1]["reliable_updates"],
                            "fp64": st64["iterations"]},
             "true_rel_resid": {"mixed": stats[-1]["true_rel_resid"], "fp64": st64["true_rel_resid"]},
@@ -446,7 +464,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--inner", default="f32_12", choices=["f32", "f32_12", "f16_12", "bf16_12"])
+    ap.add_argument("--inner", default="i16_12", choices=["f32", "f32_12", "f16_12", "bf16_12", "i16_12"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extras", action="store_true", help="skip the HMC, batch and iteration-scan numbers")
     ap.add_argument("--ref-site-fraction", type=int, default=8)
@@ -455,7 +473,7 @@ def main():
     ap.add_argument("--kernel-only", default=None, choices=["dslash", "k1", "k2", "k3", "batch"],
                     help="profiling target: only launch this kernel (precision --prec); batch: a 12-RHS "
                          "batched solve of --steps iterations")
-    ap.add_argument("--prec", default="f32_12", choices=["f64", "f32", "f32_12", "f16_12", "bf16_12"])
+    ap.add_argument("--prec", default="f32_12", choices=["f64", "f32", "f32_12", "f16_12", "bf16_12", "i16_12"])
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
     args = ap.parse_args()
     if args.impl == "reference":

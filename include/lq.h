@@ -73,9 +73,13 @@ typedef enum {
  *   LQ_BF16_12  as LQ_F16_12 with BF16 storage
  *   LQ_DF64     links and spinors as double-float pairs (hi + lo FP32, ~48 bits),
  *               double-float arithmetic on the FP32 pipe: operator applications only
- *               (lq_apply_M, lq_apply_MdagM, lq_time_dslash); the solver uses it for
- *               its intermediate reliable updates */
-typedef enum { LQ_F64 = 0, LQ_F32 = 1, LQ_F32_12 = 2, LQ_F16_12 = 3, LQ_BF16_12 = 4, LQ_DF64 = 5 } lq_prec;
+ *               (lq_apply_M, lq_apply_MdagM, lq_time_dslash); the solver can use it for
+ *               its intermediate reliable updates (LQ_OPT_DF64_UPDATES)
+ *   LQ_I16_12   16-bit fixed point: links (12 reals) as q/32767, spinors as q/32767
+ *               times a per-site FP32 norm (15 bits relative to the site maximum),
+ *               FP32 arithmetic */
+typedef enum { LQ_F64 = 0, LQ_F32 = 1, LQ_F32_12 = 2, LQ_F16_12 = 3, LQ_BF16_12 = 4, LQ_DF64 = 5,
+               LQ_I16_12 = 6 } lq_prec;
 
 typedef struct {
   int iterations;           /* CG iterations (inner iterations for a mixed solve) */

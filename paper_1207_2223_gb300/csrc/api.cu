@@ -49,7 +49,8 @@ lq_status alloc_field(lq_ctx* c, Field& f, SStore s) {
   if (f.data) return LQ_OK;
   f.store = s;
   LQ_CUDA(c, cudaMalloc(&f.data, spinor_bytes(s, c->geo.V)));
-  if (s == SStore::F16 || s == SStore::BF16) LQ_CUDA(c, cudaMalloc(&f.norm, sizeof(float) * c->geo.V));
+  if (s == SStore::F16 || s == SStore::BF16 || s == SStore::I16)
+    LQ_CUDA(c, cudaMalloc(&f.norm, sizeof(float) * c->geo.V));
   return LQ_OK;
 }
 
@@ -73,11 +74,12 @@ lq_status require_gauge(lq_ctx* c, int prec) {
 }
 
 lq_status check_prec(lq_ctx* c, int prec) {
-  if (prec < LQ_F64 || prec > LQ_DF64) return fail(c, LQ_ERR_ARG, "unknown precision");
+  if (prec < LQ_F64 || prec > LQ_I16_12) return fail(c, LQ_ERR_ARG, "unknown precision");
   return LQ_OK;
 }
 lq_status check_inner(lq_ctx* c, int prec) {
-  if (prec < LQ_F64 || prec > LQ_BF16_12) return fail(c, LQ_ERR_ARG, "unknown or unsupported solver precision");
+  if (prec < LQ_F64 || prec > LQ_I16_12 || prec == LQ_DF64)
+    return fail(c, LQ_ERR_ARG, "unknown or unsupported solver precision");
   return LQ_OK;
 }
 
@@ -169,7 +171,7 @@ lq_status read_state(lq_ctx* c) {
 double reliable_delta2(int inner) {
   switch (inner) {
     case LQ_BF16_12: return 1e-2;
-    case LQ_F16_12: return 1e-4;
+    case LQ_F16_12: case LQ_I16_12: return 1e-4;
     default: return 1e-4;
   }
 }
@@ -473,7 +475,7 @@ lq_status lq_destroy(lq_ctx* c) {
   for (double* d : {c->mom, c->mom0, c->force, c->stage_mom})
     if (d) cudaFree(d);
   if (c->gauge_old) cudaFree(c->gauge_old);
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < kNumSStore; ++k) {
     free_field(c->r_lo[k]);
     free_field(c->p_lo[k]);
     free_field(c->t_lo[k]);

@@ -22,6 +22,7 @@ void apply_M_prec(const Geom& g, int prec, const void* gauge, SpinorRef in, Spin
     case LQ_F16_12: apply_one<float, GStore::F16_12, SStore::F16>(g, gauge, in, out, kappa, dagger, stream); break;
     case LQ_BF16_12: apply_one<float, GStore::BF16_12, SStore::BF16>(g, gauge, in, out, kappa, dagger, stream); break;
     case LQ_DF64: apply_one<df64, GStore::DF64_18, SStore::DF64>(g, gauge, in, out, kappa, dagger, stream); break;
+    case LQ_I16_12: apply_one<float, GStore::I16_12, SStore::I16>(g, gauge, in, out, kappa, dagger, stream); break;
   }
 }
 

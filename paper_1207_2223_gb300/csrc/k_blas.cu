@@ -108,6 +108,7 @@ __global__ void state_after_residual_kernel(SolverState* st, int restart) {
     case SStore::F16: { constexpr SStore SS = SStore::F16; CALL; } break;   \
     case SStore::BF16: { constexpr SStore SS = SStore::BF16; CALL; } break; \
     case SStore::DF64: { constexpr SStore SS = SStore::DF64; CALL; } break; \
+    case SStore::I16: { constexpr SStore SS = SStore::I16; CALL; } break;   \
   }
 
 void launch_solver_init(const Geom& g, SpinorRef phi64, SStore sx, SpinorRef x, SStore sr, SpinorRef r,

@@ -54,6 +54,7 @@ void cg64_true_residual(lq_ctx* c, double kappa, int store_lo_prec, cudaStream_t
     case SStore::F32: residual_lo<SStore::F32>(c, kappa, rlo, stream); break;
     case SStore::F16: residual_lo<SStore::F16>(c, kappa, rlo, stream); break;
     case SStore::BF16: residual_lo<SStore::BF16>(c, kappa, rlo, stream); break;
+    case SStore::I16: residual_lo<SStore::I16>(c, kappa, rlo, stream); break;
     default: break;
   }
 }

@@ -85,6 +85,7 @@ void df_reliable_update(lq_ctx* c, double kappa, int inner_prec, cudaStream_t st
     case SStore::F32: ru<SStore::F32>(c, kappa, stream); break;
     case SStore::F16: ru<SStore::F16>(c, kappa, stream); break;
     case SStore::BF16: ru<SStore::BF16>(c, kappa, stream); break;
+    case SStore::I16: ru<SStore::I16>(c, kappa, stream); break;
     default: break;
   }
 }
@@ -96,6 +97,7 @@ void launch_inner_restart_df(const Geom& g, SpinorRef src, SStore s, SpinorRef x
     case SStore::F32: inner_restart_df_kernel<SStore::F32><<<grid, kBS, 0, stream>>>(g.V, src, x, r, p); break;
     case SStore::F16: inner_restart_df_kernel<SStore::F16><<<grid, kBS, 0, stream>>>(g.V, src, x, r, p); break;
     case SStore::BF16: inner_restart_df_kernel<SStore::BF16><<<grid, kBS, 0, stream>>>(g.V, src, x, r, p); break;
+    case SStore::I16: inner_restart_df_kernel<SStore::I16><<<grid, kBS, 0, stream>>>(g.V, src, x, r, p); break;
     default: break;
   }
 }

@@ -39,6 +39,7 @@ void cglo_step(lq_ctx* c, int prec, int which, double kappa, cudaStream_t stream
     case LQ_F32_12: step<GStore::F32_12, SStore::F32>(c, gauge, which, kappa, stream); break;
     case LQ_F16_12: step<GStore::F16_12, SStore::F16>(c, gauge, which, kappa, stream); break;
     case LQ_BF16_12: step<GStore::BF16_12, SStore::BF16>(c, gauge, which, kappa, stream); break;
+    case LQ_I16_12: step<GStore::I16_12, SStore::I16>(c, gauge, which, kappa, stream); break;
     default: break;
   }
 }
@@ -50,6 +51,7 @@ void cglo_iteration(lq_ctx* c, int prec, double kappa, cudaStream_t stream) {
     case LQ_F32_12: iteration<GStore::F32_12, SStore::F32>(c, gauge, kappa, stream); break;
     case LQ_F16_12: iteration<GStore::F16_12, SStore::F16>(c, gauge, kappa, stream); break;
     case LQ_BF16_12: iteration<GStore::BF16_12, SStore::BF16>(c, gauge, kappa, stream); break;
+    case LQ_I16_12: iteration<GStore::I16_12, SStore::I16>(c, gauge, kappa, stream); break;
     default: break;
   }
 }

@@ -66,6 +66,15 @@ __global__ void convert_gauge_kernel(int V, const double2* __restrict__ soa64, v
         const df64 a(u[c].x), b(u[c].y);
         o[(size_t)c * V + s] = make_float4(a.hi, a.lo, b.hi, b.lo);
       }
+    } else if constexpr (G == GStore::I16_12) {
+      uint2* o = static_cast<uint2*>(out) + (size_t)mu * 3 * V;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        uint2 w;
+        w.x = q16_from2((float)u[2 * k].x * kQ16, (float)u[2 * k].y * kQ16);
+        w.y = q16_from2((float)u[2 * k + 1].x * kQ16, (float)u[2 * k + 1].y * kQ16);
+        o[(size_t)k * V + s] = w;
+      }
     } else if constexpr (G == GStore::F32_18) {
       float2* o = static_cast<float2*>(out) + (size_t)mu * 9 * V;
 #pragma unroll
@@ -129,6 +138,7 @@ void launch_convert_gauge(const Geom& g, const void* soa64, GStore dst, void* ou
     case GStore::F16_12: convert_gauge_kernel<GStore::F16_12><<<grid, kBS, 0, st>>>(g.V, in, out); break;
     case GStore::BF16_12: convert_gauge_kernel<GStore::BF16_12><<<grid, kBS, 0, st>>>(g.V, in, out); break;
     case GStore::DF64_18: convert_gauge_kernel<GStore::DF64_18><<<grid, kBS, 0, st>>>(g.V, in, out); break;
+    case GStore::I16_12: convert_gauge_kernel<GStore::I16_12><<<grid, kBS, 0, st>>>(g.V, in, out); break;
   }
 }
 
@@ -157,6 +167,7 @@ void launch_pack_spinor(const Geom& g, const double* canon, SStore s, SpinorRef 
     case SStore::F16: pack_spinor_kernel<SStore::F16><<<grid, kBS, 0, st>>>(g.V, canon, out); break;
     case SStore::BF16: pack_spinor_kernel<SStore::BF16><<<grid, kBS, 0, st>>>(g.V, canon, out); break;
     case SStore::DF64: pack_spinor_kernel<SStore::DF64><<<grid, kBS, 0, st>>>(g.V, canon, out); break;
+    case SStore::I16: pack_spinor_kernel<SStore::I16><<<grid, kBS, 0, st>>>(g.V, canon, out); break;
   }
 }
 void launch_unpack_spinor(const Geom& g, SStore s, SpinorRef in, double* canon, cudaStream_t st) {
@@ -167,6 +178,7 @@ void launch_unpack_spinor(const Geom& g, SStore s, SpinorRef in, double* canon, 
     case SStore::F16: unpack_spinor_kernel<SStore::F16><<<grid, kBS, 0, st>>>(g.V, in, canon); break;
     case SStore::BF16: unpack_spinor_kernel<SStore::BF16><<<grid, kBS, 0, st>>>(g.V, in, canon); break;
     case SStore::DF64: unpack_spinor_kernel<SStore::DF64><<<grid, kBS, 0, st>>>(g.V, in, canon); break;
+    case SStore::I16: unpack_spinor_kernel<SStore::I16><<<grid, kBS, 0, st>>>(g.V, in, canon); break;
   }
 }
 

@@ -15,6 +15,9 @@
 //   gauge F16_12 / BF16_12  uint2 [4][3][V]  rows 0, 1 only, 4 reals per chunk
 //   spinor DF64  float4 [12][V]           (re.hi, re.lo, im.hi, im.lo) double-float
 //   gauge DF64_18 float4 [4][9][V]        double-float, 18 reals
+//   spinor I16   uint4 [3][V] + float norm[V]: 16-bit fixed point, value = q / 32767 * norm,
+//                stored as u = q + 32768
+//   gauge I16_12 uint2 [4][3][V]          rows 0, 1 as 16-bit fixed point, value = q / 32767
 // Links stored with 12 reals are rebuilt on the fly with
 // row 2 = conj(row 0 x row 1), exact for SU(3).  The antiperiodic time
 // boundary is applied as a sign on the hop, never folded into links, so
@@ -61,8 +64,32 @@ template <typename T> __device__ __forceinline__ cplx<T> conjg(cplx<T> a) { retu
 template <typename T> __device__ __forceinline__ T norm2(cplx<T> a) { return a.re * a.re + a.im * a.im; }
 
 // ---------------------------------------------------------------- formats
-enum class SStore : int { F64 = 0, F32 = 1, F16 = 2, BF16 = 3, DF64 = 4 };
-enum class GStore : int { F64_18 = 0, F32_18 = 1, F32_12 = 2, F16_12 = 3, BF16_12 = 4, DF64_18 = 5 };
+enum class SStore : int { F64 = 0, F32 = 1, F16 = 2, BF16 = 3, DF64 = 4, I16 = 5 };
+enum class GStore : int { F64_18 = 0, F32_18 = 1, F32_12 = 2, F16_12 = 3, BF16_12 = 4, DF64_18 = 5, I16_12 = 6 };
+
+// 16-bit fixed point, value q / 32767 (times the site norm for spinors),
+// stored offset-binary: u = q + 32768 in 16 bits.  A byte permutation builds
+// the float bits 0x4B000000 | u, i.e. the float 2^23 + u exactly (floats in
+// [2^23, 2^24) are the integers), so decoding is one PRMT and one FADD.
+// Encoding rounds x + 2^23 + 32768 to an integer in the same binade and keeps
+// the low 16 bits of the two results with one PRMT.
+constexpr float kQ16 = 32767.0f;
+constexpr float kQ16Inv = 1.0f / 32767.0f;
+constexpr float kQ16Bias = 8421376.0f;   // 2^23 + 32768
+__device__ __forceinline__ float2 q16_to2(uint32_t w) {   // raw q values
+  const float lo = __int_as_float((int)__byte_perm(w, 0x4B00u, 0x5410u)) - kQ16Bias;
+  const float hi = __int_as_float((int)__byte_perm(w, 0x4B00u, 0x5432u)) - kQ16Bias;
+  return make_float2(lo, hi);
+}
+__device__ __forceinline__ float2 q16_to2(uint32_t w, float scale) {
+  const float2 r = q16_to2(w);
+  return make_float2(r.x * scale, r.y * scale);
+}
+__device__ __forceinline__ uint32_t q16_from2(float a, float b) {   // a, b in [-32767, 32767]
+  const uint32_t ua = (uint32_t)__float_as_int(a + kQ16Bias);
+  const uint32_t ub = (uint32_t)__float_as_int(b + kQ16Bias);
+  return __byte_perm(ua, ub, 0x5410u);
+}
 
 // Conversions of a double-float to the arithmetic type of a kernel.
 template <typename T> __device__ __forceinline__ T from_df(df64 v) { return (T)v; }
@@ -109,6 +136,7 @@ template <> struct SpinorTraits<SStore::F32> { using half_t = void; };
 template <> struct SpinorTraits<SStore::F16> { using half_t = __half; };
 template <> struct SpinorTraits<SStore::BF16> { using half_t = __nv_bfloat16; };
 template <> struct SpinorTraits<SStore::DF64> { using half_t = void; };
+template <> struct SpinorTraits<SStore::I16> { using half_t = void; };
 
 // ----------------------------------------------------------- spinor I/O
 // RO = true: the field is read-only for the whole kernel, so loads may use
@@ -137,6 +165,18 @@ __device__ __forceinline__ void load_spinor(const SpinorRef& f, int V, int s, cp
       float4 w = ld<RO>(p + (size_t)k * V + s);
       v[2 * k] = {(T)w.x, (T)w.y}; v[2 * k + 1] = {(T)w.z, (T)w.w};
     }
+  } else if constexpr (S == SStore::I16) {
+    const uint4* p = static_cast<const uint4*>(f.p);
+    const float sc = ld<RO>(f.norm + s) * kQ16Inv;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 w = ld<RO>(p + (size_t)k * V + s);
+      float2 a = q16_to2(w.x, sc), b = q16_to2(w.y, sc), c = q16_to2(w.z, sc), e = q16_to2(w.w, sc);
+      v[4 * k + 0] = {(T)a.x, (T)a.y};
+      v[4 * k + 1] = {(T)b.x, (T)b.y};
+      v[4 * k + 2] = {(T)c.x, (T)c.y};
+      v[4 * k + 3] = {(T)e.x, (T)e.y};
+    }
   } else {
     using H = typename SpinorTraits<S>::half_t;
     const uint4* p = static_cast<const uint4*>(f.p);
@@ -161,6 +201,19 @@ __device__ __forceinline__ T load_spinor_raw(const SpinorRef& f, int V, int s, c
   if constexpr (S == SStore::F64 || S == SStore::F32 || S == SStore::DF64) {
     load_spinor<S, T>(f, V, s, v);
     return (T)1;
+  } else if constexpr (S == SStore::I16) {
+    const uint4* p = static_cast<const uint4*>(f.p);
+    const float nrm = __ldg(f.norm + s);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 w = __ldg(p + (size_t)k * V + s);
+      float2 a = q16_to2(w.x), b = q16_to2(w.y), c = q16_to2(w.z), e = q16_to2(w.w);
+      v[4 * k + 0] = {(T)a.x, (T)a.y};
+      v[4 * k + 1] = {(T)b.x, (T)b.y};
+      v[4 * k + 2] = {(T)c.x, (T)c.y};
+      v[4 * k + 3] = {(T)e.x, (T)e.y};
+    }
+    return (T)(nrm * kQ16Inv);
   } else {
     using H = typename SpinorTraits<S>::half_t;
     const uint4* p = static_cast<const uint4*>(f.p);
@@ -196,6 +249,22 @@ __device__ __forceinline__ void store_spinor(const SpinorRef& f, int V, int s, c
 #pragma unroll
     for (int k = 0; k < 6; ++k)
       p[(size_t)k * V + s] = make_float4((float)v[2 * k].re, (float)v[2 * k].im, (float)v[2 * k + 1].re, (float)v[2 * k + 1].im);
+  } else if constexpr (S == SStore::I16) {
+    uint4* p = static_cast<uint4*>(f.p);
+    float m = 0.f;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) m = fmaxf(m, fmaxf(fabsf((float)v[c].re), fabsf((float)v[c].im)));
+    const float inv = m > 0.f ? kQ16 / m : 0.f;
+    f.norm[s] = m;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 w;
+      w.x = q16_from2((float)v[4 * k + 0].re * inv, (float)v[4 * k + 0].im * inv);
+      w.y = q16_from2((float)v[4 * k + 1].re * inv, (float)v[4 * k + 1].im * inv);
+      w.z = q16_from2((float)v[4 * k + 2].re * inv, (float)v[4 * k + 2].im * inv);
+      w.w = q16_from2((float)v[4 * k + 3].re * inv, (float)v[4 * k + 3].im * inv);
+      p[(size_t)k * V + s] = w;
+    }
   } else {
     using H = typename SpinorTraits<S>::half_t;
     uint4* p = static_cast<uint4*>(f.p);
@@ -224,6 +293,7 @@ template <> struct GaugeTraits<GStore::F32_12> { using half_t = void; };
 template <> struct GaugeTraits<GStore::F16_12> { using half_t = __half; };
 template <> struct GaugeTraits<GStore::BF16_12> { using half_t = __nv_bfloat16; };
 template <> struct GaugeTraits<GStore::DF64_18> { using half_t = void; };
+template <> struct GaugeTraits<GStore::I16_12> { using half_t = void; };
 
 template <typename T>
 __device__ __forceinline__ void reconstruct_row2(cplx<T> u[9]) {
@@ -249,6 +319,15 @@ __device__ __forceinline__ void load_link(const GaugeRef& g, int V, int mu, int 
     const float2* p = static_cast<const float2*>(g.p) + (size_t)mu * 9 * V;
 #pragma unroll
     for (int c = 0; c < 9; ++c) { float2 w = __ldg(p + (size_t)c * V + s); u[c] = {(T)w.x, (T)w.y}; }
+  } else if constexpr (G == GStore::I16_12) {
+    const uint2* p = static_cast<const uint2*>(g.p) + (size_t)mu * 3 * V;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint2 w = __ldg(p + (size_t)k * V + s);
+      float2 a = q16_to2(w.x, kQ16Inv), b = q16_to2(w.y, kQ16Inv);
+      u[2 * k] = {(T)a.x, (T)a.y}; u[2 * k + 1] = {(T)b.x, (T)b.y};
+    }
+    reconstruct_row2(u);
   } else if constexpr (G == GStore::F32_12) {
     const float4* p = static_cast<const float4*>(g.p) + (size_t)mu * 3 * V;
 #pragma unroll

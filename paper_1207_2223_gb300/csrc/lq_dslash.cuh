@@ -72,7 +72,7 @@ __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, cons
     cplx<T> h0[3], h1[3];
     project<MU, SF>(p, h0, h1);
     if (MU == 3 && geo.antiperiodic && c[3] == geo.L[3] - 1) sc = -sc;
-    if (SI == SStore::F16 || SI == SStore::BF16 || (MU == 3 && geo.antiperiodic)) {
+    if (SI == SStore::F16 || SI == SStore::BF16 || SI == SStore::I16 || (MU == 3 && geo.antiperiodic)) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) { h0[k] = sc * h0[k]; h1[k] = sc * h1[k]; }
     }
@@ -90,7 +90,7 @@ __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, cons
     cplx<T> h0[3], h1[3];
     project<MU, -SF>(p, h0, h1);
     if (MU == 3 && geo.antiperiodic && c[3] == 0) sc = -sc;
-    if (SI == SStore::F16 || SI == SStore::BF16 || (MU == 3 && geo.antiperiodic)) {
+    if (SI == SStore::F16 || SI == SStore::BF16 || SI == SStore::I16 || (MU == 3 && geo.antiperiodic)) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) { h0[k] = sc * h0[k]; h1[k] = sc * h1[k]; }
     }

@@ -13,7 +13,8 @@
 
 namespace lq {
 
-constexpr int kNumPrec = 6;   // LQ_F64 .. LQ_DF64
+constexpr int kNumPrec = 7;   // LQ_F64 .. LQ_I16_12
+constexpr int kNumSStore = 6;
 
 inline GStore gauge_store_of(int prec) {
   switch (prec) {
@@ -22,6 +23,7 @@ inline GStore gauge_store_of(int prec) {
     case LQ_F32_12: return GStore::F32_12;
     case LQ_F16_12: return GStore::F16_12;
     case LQ_DF64: return GStore::DF64_18;
+    case LQ_I16_12: return GStore::I16_12;
     default: return GStore::BF16_12;
   }
 }
@@ -31,6 +33,7 @@ inline SStore spinor_store_of(int prec) {
     case LQ_F32: case LQ_F32_12: return SStore::F32;
     case LQ_F16_12: return SStore::F16;
     case LQ_DF64: return SStore::DF64;
+    case LQ_I16_12: return SStore::I16;
     default: return SStore::BF16;
   }
 }
@@ -60,8 +63,8 @@ struct lq_ctx {
 
   // gauge field: FP64 master copy and lazily built low-precision copies
   void* gauge64 = nullptr;
-  void* gauge_lo[lq::kNumPrec] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  bool gauge_lo_valid[lq::kNumPrec] = {false, false, false, false, false, false};
+  void* gauge_lo[lq::kNumPrec] = {};
+  bool gauge_lo_valid[lq::kNumPrec] = {};
   bool gauge_set = false;
 
   // canonical-layout staging buffers (device)
@@ -72,7 +75,7 @@ struct lq_ctx {
   // FP64 solver fields
   lq::Field phi64, x64, r64, p64, t64, tmp64;
   // low-precision solver fields, one set per storage format (indexed by SStore)
-  lq::Field r_lo[5], p_lo[5], t_lo[5], x_lo[5];
+  lq::Field r_lo[lq::kNumSStore], p_lo[lq::kNumSStore], t_lo[lq::kNumSStore], x_lo[lq::kNumSStore];
   // double-float reliable updates: phi, the accumulated solution, M x, the residual
   lq::Field phi_df, x_df, tmp_df, r_df;
 

@@ -14,9 +14,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblq.so")
 
 LQ_OK, LQ_ERR_ARG, LQ_ERR_SHAPE, LQ_ERR_CUDA, LQ_ERR_NOT_CONVERGED, LQ_ERR_NAN, LQ_ERR_STATE = range(7)
-LQ_F64, LQ_F32, LQ_F32_12, LQ_F16_12, LQ_BF16_12, LQ_DF64 = range(6)
+LQ_F64, LQ_F32, LQ_F32_12, LQ_F16_12, LQ_BF16_12, LQ_DF64, LQ_I16_12 = range(7)
 PRECISIONS = {"f64": LQ_F64, "f32": LQ_F32, "f32_12": LQ_F32_12, "f16_12": LQ_F16_12, "bf16_12": LQ_BF16_12,
-              "df64": LQ_DF64}
+              "df64": LQ_DF64, "i16_12": LQ_I16_12}
 
 
 class LQError(RuntimeError):

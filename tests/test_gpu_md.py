@@ -122,7 +122,7 @@ def test_trajectory_small_preset_fp64(lq):
     assert np.max(np.abs(Ug - ref["U"])) < 1e-10
 
 
-@pytest.mark.parametrize("prec", [1, 2, 3])
+@pytest.mark.parametrize("prec", [1, 2, 3, 6])
 def test_trajectory_mixed_precision_solves(lq, prec):
     """Same trajectory with mixed-precision solves (FP64 true residual 1e-10 each)."""
     dims = (4, 4, 4, 4)

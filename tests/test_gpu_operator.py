@@ -11,8 +11,9 @@ pytestmark = pytest.mark.gpu
 # FP64 bound: relative 1e-12.  Lower precisions: relative error of the
 # storage format (FP32 2^-24, FP16 2^-11 relative to the site norm, BF16
 # 2^-8) times a small factor for the ~100 operations per output.
-# Double-float (LQ_DF64, ~48-bit significands): 1e-12 as for FP64.
-TOL = {0: 1e-12, 1: 2e-6, 2: 2e-6, 3: 2e-3, 4: 1.5e-2, 5: 1e-12}
+# Double-float (LQ_DF64, ~48-bit significands): 1e-12 as for FP64.  16-bit fixed point
+# (LQ_I16_12): rounding 2^-16 of the site maximum for spinors and of 1 for links.
+TOL = {0: 1e-12, 1: 2e-6, 2: 2e-6, 3: 2e-3, 4: 1.5e-2, 5: 1e-12, 6: 2e-4}
 
 SHAPES = [(4, 4, 4, 4), (2, 2, 2, 2), (6, 4, 2, 6), (3, 5, 2, 7), (8, 8, 8, 16)]
 
@@ -45,7 +46,7 @@ def test_apply_M_f64(lq, dims, dagger):
     assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("prec", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("prec", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_apply_M_low_precision(lq, prec, dagger):
     dims = (4, 4, 6, 8)
@@ -137,7 +138,7 @@ def test_full_size_sampled_sites(lq):
         del Ud
         pin = dev(psi)
         out = torch.empty_like(pin)
-        for prec in (0, 1, 3, 5):
+        for prec in (0, 1, 3, 5, 6):
             for d in (False, True):
                 lq.lq_apply_M(ctx, out, pin, 0.156, d, prec)
                 got = host(out)[sites]

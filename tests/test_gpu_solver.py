@@ -22,7 +22,7 @@ X_TOL = 1e-6
 
 @pytest.mark.parametrize("dims,kappa,sigma", [((4, 4, 4, 4), 0.15, 0.3), ((6, 4, 2, 6), 0.155, 0.3),
                                               ((8, 8, 8, 8), 0.156, 0.25)])
-@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4, 6])
 def test_solve_matches_oracle(lq, dims, kappa, sigma, prec):
     lat = Lattice(dims)
     U = gauge_exp_iA(lat, sigma, 2)
@@ -118,7 +118,7 @@ def test_full_size_mixed_and_f64_solves(lq):
     try:
         lq.lq_gauge_set(ctx, dev(U))
         xs = {}
-        for prec in (lq.LQ_F16_12, lq.LQ_F64):
+        for prec in (lq.LQ_F16_12, lq.LQ_I16_12, lq.LQ_F64):
             x = torch.zeros_like(phi)
             status, st = lq.lq_solve_MdagM(ctx, x, phi, 0.156, 1e-10, 20000, prec, 50)
             assert status == lq.LQ_OK and st["true_rel_resid"] <= 1e-10, st
