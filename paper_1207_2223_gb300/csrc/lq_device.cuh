@@ -76,14 +76,15 @@ enum class GStore : int { F64_18 = 0, F32_18 = 1, F32_12 = 2, F16_12 = 3, BF16_1
 constexpr float kQ16 = 32767.0f;
 constexpr float kQ16Inv = 1.0f / 32767.0f;
 constexpr float kQ16Bias = 8421376.0f;   // 2^23 + 32768
+// The two halves of a word are decoded with one packed FP32x2 add (and scaled
+// with one packed multiply): Blackwell issues these as single instructions.
 __device__ __forceinline__ float2 q16_to2(uint32_t w) {   // raw q values
-  const float lo = __int_as_float((int)__byte_perm(w, 0x4B00u, 0x5410u)) - kQ16Bias;
-  const float hi = __int_as_float((int)__byte_perm(w, 0x4B00u, 0x5432u)) - kQ16Bias;
-  return make_float2(lo, hi);
+  const float2 b = make_float2(__int_as_float((int)__byte_perm(w, 0x4B00u, 0x5410u)),
+                               __int_as_float((int)__byte_perm(w, 0x4B00u, 0x5432u)));
+  return __fadd2_rn(b, make_float2(-kQ16Bias, -kQ16Bias));
 }
 __device__ __forceinline__ float2 q16_to2(uint32_t w, float scale) {
-  const float2 r = q16_to2(w);
-  return make_float2(r.x * scale, r.y * scale);
+  return __fmul2_rn(q16_to2(w), make_float2(scale, scale));
 }
 __device__ __forceinline__ uint32_t q16_from2(float a, float b) {   // a, b in [-32767, 32767]
   const uint32_t ua = (uint32_t)__float_as_int(a + kQ16Bias);

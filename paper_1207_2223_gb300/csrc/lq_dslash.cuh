@@ -45,6 +45,13 @@ struct SolverState {
 
 struct NoEpiState {};
 
+// s * a; FP32 complex numbers with one packed FP32x2 multiply
+template <typename T> __device__ __forceinline__ cplx<T> scale_c(T s, cplx<T> a) { return s * a; }
+template <> __device__ __forceinline__ cplx<float> scale_c<float>(float s, cplx<float> a) {
+  const float2 r = __fmul2_rn(make_float2(a.re, a.im), make_float2(s, s));
+  return {r.x, r.y};
+}
+
 // Where the spinor of site n lives: one field of V sites (Single), or one
 // system of a batch whose right-hand sides are interleaved fastest inside a
 // field shared by all systems (Batched: element off + n R + r, chunk stride
@@ -74,7 +81,7 @@ __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, cons
     if (MU == 3 && geo.antiperiodic && c[3] == geo.L[3] - 1) sc = -sc;
     if (SI == SStore::F16 || SI == SStore::BF16 || SI == SStore::I16 || (MU == 3 && geo.antiperiodic)) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) { h0[k] = sc * h0[k]; h1[k] = sc * h1[k]; }
+      for (int k = 0; k < 3; ++k) { h0[k] = scale_c(sc, h0[k]); h1[k] = scale_c(sc, h1[k]); }
     }
     cplx<T> u[9];
     load_link<G, T>(U, geo.V, MU, s, u);
@@ -92,7 +99,7 @@ __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, cons
     if (MU == 3 && geo.antiperiodic && c[3] == 0) sc = -sc;
     if (SI == SStore::F16 || SI == SStore::BF16 || SI == SStore::I16 || (MU == 3 && geo.antiperiodic)) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) { h0[k] = sc * h0[k]; h1[k] = sc * h1[k]; }
+      for (int k = 0; k < 3; ++k) { h0[k] = scale_c(sc, h0[k]); h1[k] = scale_c(sc, h1[k]); }
     }
     cplx<T> u[9];
     load_link<G, T>(U, geo.V, MU, n, u);
