@@ -56,8 +56,10 @@ DSLASH_FLOPS = 1368
 # dram__bytes_write.sum over sites), valid for the kernel sources with this
 # hash; see profiles/.  Null when the kernel changed since the capture.
 NCU_TRAFFIC = {
-    # profiles/cg_pass2_f32_12_32x32x32x32.md: 617.80 MB read + 173.37 MB written over 32^4 sites
-    "f32_12": {"bytes_per_site": 754.5, "src": "6a8892349e2b3f82"},
+    # profiles/cg_pass2_i16_12_32x32x32x32.md
+    "i16_12": {"bytes_per_site": 384.2, "src": "2a3cbf4942624785"},
+    # profiles/cg_pass2_f32_12_32x32x32x32.md
+    "f32_12": {"bytes_per_site": 754.9, "src": "2a3cbf4942624785"},
 }
 
 
@@ -146,25 +148,34 @@ def measure_extras(lq, torch, dev):
     import numpy as np
     from synth import Lattice, gauge_exp_iA, source, momenta, chi_noise, metropolis_uniform
     out = {}
-    # HMC: 16^4, beta 5.6, kappa 0.155, 20 leapfrog steps, tau 1, reunitarised exp(iA) start
-    dims = (16, 16, 16, 16)
-    lat = Lattice(dims)
-    U = torch.from_numpy(gauge_exp_iA(lat, 0.3, 1, reunitarise=True)).to(dev)
-    p0 = torch.from_numpy(momenta(lat, 1)).to(dev)
-    chi = torch.from_numpy(chi_noise(lat, 1)).to(dev)
-    u = metropolis_uniform(1)
-    hmc = {}
-    for name, prec in (("f64", lq.LQ_F64), ("mixed_f32_12", lq.LQ_F32_12)):
-        ctx = lq.lq_create(dims, True, torch.cuda.current_stream(dev).cuda_stream)
-        try:
-            lq.lq_gauge_set(ctx, U)
-            r = lq.lq_hmc_trajectory(ctx, p0.clone(), chi, u, 5.6, 0.155, 20, 1.0, 1e-10, 20000, prec, 50)
-        finally:
-            lq.lq_destroy(ctx)
-        hmc[name] = {"seconds": r["seconds"], "trajectories_per_s": 1.0 / r["seconds"], "dH": r["dH"],
-                     "accepted": r["accepted"], "solves": r["solves"], "cg_iterations": r["cg_iterations"],
-                     "plaquette": r["plaquette"]}
-    out["hmc_16x16x16x16"] = hmc
+    # HMC trajectories (beta 5.6, kappa 0.155, 20 leapfrog steps, tau 1, reunitarised exp(iA)
+    # start, sigma 0.3) with the per-routine device-time split, 8^4 to 24^4; FP64 and mixed
+    # solves at 16^4
+    for dims in ((8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 24)):
+        lat = Lattice(dims)
+        U = torch.from_numpy(gauge_exp_iA(lat, 0.3, 1, reunitarise=True)).to(dev)
+        p0 = torch.from_numpy(momenta(lat, 1)).to(dev)
+        chi = torch.from_numpy(chi_noise(lat, 1)).to(dev)
+        u = metropolis_uniform(1)
+        hmc = {}
+        runs = (("f64", lq.LQ_F64), ("mixed_i16_12", lq.LQ_I16_12)) if dims[0] == 16 else (("mixed_i16_12", lq.LQ_I16_12),)
+        for name, prec in runs:
+            ctx = lq.lq_create(dims, True, torch.cuda.current_stream(dev).cuda_stream)
+            try:
+                lq.lq_gauge_set(ctx, U)
+                r = lq.lq_hmc_trajectory(ctx, p0.clone(), chi, u, 5.6, 0.155, 20, 1.0, 1e-10, 20000, prec, 50)
+            finally:
+                lq.lq_destroy(ctx)
+            dev_total = r["seconds_solve"] + r["seconds_gauge_force"] + r["seconds_fermion_force"] + \
+                r["seconds_link_update"]
+            hmc[name] = {"seconds": r["seconds"], "trajectories_per_s": 1.0 / r["seconds"], "dH": r["dH"],
+                         "accepted": r["accepted"], "solves": r["solves"], "cg_iterations": r["cg_iterations"],
+                         "plaquette": r["plaquette"],
+                         "share": {"solve": r["seconds_solve"] / dev_total,
+                                   "gauge_force": r["seconds_gauge_force"] / dev_total,
+                                   "fermion_force": r["seconds_fermion_force"] / dev_total,
+                                   "link_update": r["seconds_link_update"] / dev_total}}
+        out["hmc_%dx%dx%dx%d" % dims] = hmc
     # batched solve: 24^4, kappa 0.155, seed 3, 12 right-hand sides sharing one gauge field
     dims = (24, 24, 24, 24)
     lat = Lattice(dims)

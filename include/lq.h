@@ -214,6 +214,11 @@ typedef struct {
   int64_t cg_iterations;     /* their total iterations */
   int64_t kernel_launches;   /* kernels launched by the call */
   double seconds;            /* host wall-clock of the call */
+  /* device time per routine (CUDA events), the paper's per-routine timing (Sec. 4) */
+  double seconds_solve;          /* CG solves (the inversions) */
+  double seconds_gauge_force;    /* gauge force fused with the momentum update */
+  double seconds_fermion_force;  /* Y = M X and the fermion force fused with the momentum update */
+  double seconds_link_update;    /* exp(i eps p) U and reunitarisation */
 } lq_traj_result;
 
 /* Average plaquette <Re tr U_P / 3> over the 6 V plaquettes (1 for U = 1);

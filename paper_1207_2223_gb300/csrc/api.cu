@@ -379,18 +379,56 @@ void gauge_changed(lq_ctx* c) {
   for (int p = 0; p < kNumPrec; ++p) c->gauge_lo_valid[p] = false;
 }
 
+// Device time of the phases of a trajectory: CUDA event pairs on the work
+// stream, summed once the trajectory has synchronised.
+struct PhaseTimer {
+  enum { kSolve, kGauge, kFermion, kLink, kN };
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[kN];
+  cudaStream_t st;
+  explicit PhaseTimer(cudaStream_t s) : st(s) {}
+  void begin(int k) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+    ev[k].emplace_back(a, b);
+  }
+  void end(int k) { cudaEventRecord(ev[k].back().second, st); }
+  double seconds(int k) {
+    double t = 0.0;
+    for (auto& p : ev[k]) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) t += ms * 1e-3;
+    }
+    return t;
+  }
+  ~PhaseTimer() {
+    for (auto& v : ev)
+      for (auto& p : v) {
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+      }
+  }
+};
+
 // p -= eps (F_gauge + F_fermion) at the current links; one solve for X = (M^dag M)^{-1} phi
-lq_status md_force_step(lq_ctx* c, const lq_hmc_params* hp, double eps, lq_traj_result* res) {
+lq_status md_force_step(lq_ctx* c, const lq_hmc_params* hp, double eps, lq_traj_result* res, PhaseTimer& tm) {
+  tm.begin(PhaseTimer::kGauge);
   launch_gauge_force(c->geo, c->gauge64, c->mom, hp->beta, eps, true, c->stream);
+  tm.end(PhaseTimer::kGauge);
   lq_solve_stats s{};
+  tm.begin(PhaseTimer::kSolve);
   lq_status st = solve_internal(c, hp->kappa, hp->tol, hp->maxiter, hp->inner_prec, hp->reliable_every, nullptr,
                                 0, &s);
+  tm.end(PhaseTimer::kSolve);
   res->solves += 1;
   res->cg_iterations += s.iterations;
   res->kernel_launches += s.kernel_launches + 3;
   if (st != LQ_OK) return st;
+  tm.begin(PhaseTimer::kFermion);
   apply_M_prec(c->geo, LQ_F64, c->gauge64, c->x64.ref(), c->y64.ref(), hp->kappa, false, c->stream);
   launch_fermion_force(c->geo, c->gauge64, c->x64.ref(), c->y64.ref(), c->mom, hp->kappa, eps, true, c->stream);
+  tm.end(PhaseTimer::kFermion);
   LQ_CUDA(c, cudaGetLastError());
   return LQ_OK;
 }
@@ -804,18 +842,23 @@ lq_status lq_hmc_trajectory(lq_ctx* c, const lq_hmc_params* hp, double* p, const
                              c->stream));
   r.kernel_launches += 4;
   // leapfrog: half step in p, then n x (full step in U, full step in p), last p step halved
+  PhaseTimer tm(c->stream);
   const double eps = hp->tau / hp->n_steps;
-  lq_status st = md_force_step(c, hp, 0.5 * eps, &r);
+  lq_status st = md_force_step(c, hp, 0.5 * eps, &r, tm);
   for (int i = 0; i < hp->n_steps && st == LQ_OK; ++i) {
+    tm.begin(PhaseTimer::kLink);
     launch_link_update(g, c->gauge64, c->mom, eps, c->stream);
+    tm.end(PhaseTimer::kLink);
     gauge_changed(c);
     r.kernel_launches += 1;
-    st = md_force_step(c, hp, i < hp->n_steps - 1 ? eps : 0.5 * eps, &r);
+    st = md_force_step(c, hp, i < hp->n_steps - 1 ? eps : 0.5 * eps, &r, tm);
   }
   if (st == LQ_OK) {
     // S_f at the end: X = (M^dag M)^{-1} phi on the new links
     lq_solve_stats s{};
+    tm.begin(PhaseTimer::kSolve);
     st = solve_internal(c, hp->kappa, hp->tol, hp->maxiter, hp->inner_prec, hp->reliable_every, nullptr, 0, &s);
+    tm.end(PhaseTimer::kSolve);
     r.solves += 1;
     r.cg_iterations += s.iterations;
     r.kernel_launches += s.kernel_launches;
@@ -858,6 +901,10 @@ lq_status lq_hmc_trajectory(lq_ctx* c, const lq_hmc_params* hp, double* p, const
   LQ_TRY(deliver_mom(c, c->mom, p));
   LQ_CUDA(c, cudaStreamSynchronize(c->stream));
   r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  r.seconds_solve = tm.seconds(PhaseTimer::kSolve);
+  r.seconds_gauge_force = tm.seconds(PhaseTimer::kGauge);
+  r.seconds_fermion_force = tm.seconds(PhaseTimer::kFermion);
+  r.seconds_link_update = tm.seconds(PhaseTimer::kLink);
   *out = r;
   return LQ_OK;
 }

@@ -44,7 +44,9 @@ class lq_traj_result(ctypes.Structure):
     _fields_ = [("dH", ctypes.c_double), ("dK", ctypes.c_double), ("dSg", ctypes.c_double),
                 ("dSf", ctypes.c_double), ("accepted", ctypes.c_int), ("plaquette", ctypes.c_double),
                 ("solves", ctypes.c_int), ("cg_iterations", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("seconds_solve", ctypes.c_double),
+                ("seconds_gauge_force", ctypes.c_double), ("seconds_fermion_force", ctypes.c_double),
+                ("seconds_link_update", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
