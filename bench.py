@@ -428,6 +428,18 @@ def run_ours(args):
         e2e_t, e2e_units = replicas.combine(e2e_local, args.steps, dev)
         e2e = {"value": e2e_units / e2e_t, "unit": "solves/s", "h2d_bytes_per_step": int(U.nbytes + phi.nbytes),
                "d2h_bytes_per_step": int(phi.nbytes)}
+        # host <-> device copy rate of pinned buffers (context for e2e)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        Ud.copy_(Uh, non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        h2d = U.nbytes / (c0.elapsed_time(c1) * 1e-3) / 1e9
+        c0.record(stream)
+        Uh.copy_(Ud, non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e["pinned_copy_gbs"] = {"h2d": h2d, "d2h": U.nbytes / (c0.elapsed_time(c1) * 1e-3) / 1e9}
 
         extras = None if args.no_extras else measure_extras(lq, torch, dev)
 
