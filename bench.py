@@ -185,15 +185,15 @@ def measure_extras(lq, torch, dev):
     try:
         lq.lq_gauge_set(ctx, U)
         x = torch.zeros_like(phis)
-        lq.lq_solve_batch([ctx], [x], [phis], [0.155], 12, 1e-10, 20000, lq.LQ_F32_12, 50)   # autotune
+        lq.lq_solve_batch([ctx], [x], [phis], [0.155], 12, 1e-10, 20000, lq.LQ_I16_12, 50)   # autotune
         t0 = time.perf_counter()
         status, st, iters, resid, _ = lq.lq_solve_batch([ctx], [x], [phis], [0.155], 12, 1e-10, 20000,
-                                                        lq.LQ_F32_12, 50)
+                                                        lq.LQ_I16_12, 50)
         tb = time.perf_counter() - t0
         t0 = time.perf_counter()
         for i in range(12):
             xs = torch.zeros_like(phis[i])
-            lq.lq_solve_MdagM(ctx, xs, phis[i], 0.155, 1e-10, 20000, lq.LQ_F32_12, 50)
+            lq.lq_solve_MdagM(ctx, xs, phis[i], 0.155, 1e-10, 20000, lq.LQ_I16_12, 50)
         ts = time.perf_counter() - t0
     finally:
         lq.lq_destroy(ctx)

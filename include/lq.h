@@ -176,8 +176,11 @@ lq_status lq_solve_MdagM(lq_ctx* ctx, double* x, const double* phi, double kappa
  * device) with nrhs right-hand sides phi[k] (device, canonical spinors stored
  * one after another: [nrhs][V_k][4][3] complex), solution x[k] (device, same
  * layout).  Right-hand sides of one system share its links, which are read
- * once per site for all of them.  Iterations run in FP32 (inner_prec LQ_F32
- * or LQ_F32_12) with FP64 reliable updates every reliable_every iterations;
+ * once per site for all of them.  Iterations run in FP32 arithmetic on the storage
+ * of inner_prec (LQ_F32, LQ_F32_12, LQ_F16_12 or LQ_I16_12) with FP64 reliable updates
+ * every reliable_every iterations (sooner when a column's iterated residual fell by 1e-2,
+ * 16-bit storage, or 1e-3, FP32; a column whose true residual turns out far above its
+ * iterated one restarts its search direction);
  * a column (system x right-hand side) whose FP64 true residual meets tol is
  * frozen.  1 <= n <= 16, 1 <= nrhs <= 16, n * nrhs <= 64.  Block size is
  * picked by timing candidates on the first call (autotuning); the iterations

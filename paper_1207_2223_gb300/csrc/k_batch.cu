@@ -54,9 +54,11 @@ struct BatchDesc {
 // Per-column solver scalars (device).
 struct BatchState {
   double rr[kMaxCols], rr_prev[kMaxCols], alpha[kMaxCols], beta[kMaxCols], phi2[kMaxCols], rr_true[kMaxCols];
+  double rr_ref[kMaxCols];   // |r|^2 right after the column's last reliable update
   int done[kMaxCols];
   int conv_iter[kMaxCols];
   double stop2;            // tol^2
+  double delta2;           // reliable update once a column's |r|^2 fell below delta2 * rr_ref
   int iter, iter_since_ru, ru_every, maxiter, halt, breakdown, hist_len, pad_;
   double* hist;            // [ncols][hist_len] relative iterated residuals
 };
@@ -128,6 +130,7 @@ struct BEpiStore64 {                        // tmp = M x (FP64)
   __device__ void finalize(const double*) const {}
 };
 
+template <SStore S>
 struct BEpiCG1 {                             // t = M p, tt = |t|^2, alpha = rr / tt
   SpinorRef t;
   int total;
@@ -135,7 +138,7 @@ struct BEpiCG1 {                             // t = M p, tt = |t|^2, alpha = rr 
   static constexpr bool REDUCE = true;
   __device__ bool halted() const { return *(volatile const int*)&st->halt; }
   template <typename T> __device__ double apply(int e, int, const cplx<T> v[12]) const {
-    store_spinor<SStore::F32, T>(t, total, e, v);
+    store_spinor<S, T>(t, total, e, v);
     T a = (T)0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) { a = fma(v[k].re, v[k].re, a); a = fma(v[k].im, v[k].im, a); }
@@ -151,6 +154,7 @@ struct BEpiCG1 {                             // t = M p, tt = |t|^2, alpha = rr 
   }
 };
 
+template <SStore S>
 struct BEpiCG2 {                             // r -= alpha M^dag t, x += alpha p, rr = |r|^2
   SpinorRef r, x, p;
   int total;
@@ -160,9 +164,9 @@ struct BEpiCG2 {                             // r -= alpha M^dag t, x += alpha p
   template <typename T> __device__ double apply(int e, int col, const cplx<T> v[12]) const {
     const T alpha = (T)st->alpha[col];
     cplx<T> rv[12], xv[12], pv[12];
-    load_spinor<SStore::F32, T, false>(r, total, e, rv);
-    load_spinor<SStore::F32, T, false>(x, total, e, xv);
-    load_spinor<SStore::F32, T>(p, total, e, pv);
+    load_spinor<S, T, false>(r, total, e, rv);
+    load_spinor<S, T, false>(x, total, e, xv);
+    load_spinor<S, T>(p, total, e, pv);
     T a = (T)0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
@@ -173,8 +177,8 @@ struct BEpiCG2 {                             // r -= alpha M^dag t, x += alpha p
       a = fma(rv[k].re, rv[k].re, a);
       a = fma(rv[k].im, rv[k].im, a);
     }
-    store_spinor<SStore::F32, T>(r, total, e, rv);
-    store_spinor<SStore::F32, T>(x, total, e, xv);
+    store_spinor<S, T>(r, total, e, rv);
+    store_spinor<S, T>(x, total, e, xv);
     return (double)a;
   }
   __device__ void finalize_cols(const double* tot, int ncols) const {
@@ -189,6 +193,7 @@ struct BEpiCG2 {                             // r -= alpha M^dag t, x += alpha p
       st->rr_prev[c] = st->rr[c];
       st->rr[c] = rr_new;
       if (rr_new > st->stop2 * st->phi2[c]) all_below = false;
+      if (rr_new < st->delta2 * st->rr_ref[c]) st->halt = 1;     // fell far: reliable update due
     }
     st->iter = it + 1;
     st->iter_since_ru += 1;
@@ -198,6 +203,7 @@ struct BEpiCG2 {                             // r -= alpha M^dag t, x += alpha p
   }
 };
 
+template <SStore S>
 struct BEpiResidual {                        // r64 = phi - M^dag tmp, r_lo = r64, rr_true = |r64|^2
   SpinorRef phi, r64, rlo;
   int total;
@@ -214,7 +220,7 @@ struct BEpiResidual {                        // r64 = phi - M^dag tmp, r_lo = r6
       a += rv[k].re * rv[k].re + rv[k].im * rv[k].im;
     }
     store_spinor<SStore::F64, double>(r64, total, e, rv);
-    store_spinor<SStore::F32, double>(rlo, total, e, rv);
+    store_spinor<S, double>(rlo, total, e, rv);
     return a;
   }
   __device__ void finalize_cols(const double* tot, int ncols) const {
@@ -227,10 +233,15 @@ struct BEpiResidual {                        // r64 = phi - M^dag tmp, r_lo = r6
         st->conv_iter[c] = st->iter;
         st->beta[c] = 0.0;
         st->alpha[c] = 0.0;
+      } else if (tot[c] > 100.0 * st->rr[c]) {
+        // the low-precision recursion drifted far below the true residual: the
+        // search direction no longer fits it, restart the column from r
+        st->beta[c] = 0.0;
       } else {
         st->beta[c] = tot[c] / st->rr_prev[c];
       }
       st->rr[c] = tot[c];
+      st->rr_ref[c] = tot[c];
     }
     st->iter_since_ru = 0;
     st->halt = 0;
@@ -296,7 +307,8 @@ __global__ void __launch_bounds__(256) batch_dslash_kernel(BatchDesc bd, SpinorR
   }
 }
 
-// p = r + beta_col p (FP32), skipped when halted unless forced
+// p = r + beta_col p (inner format), skipped when halted unless forced
+template <SStore S>
 __global__ void batch_xpay_kernel(BatchDesc bd, SpinorRef r, SpinorRef p, const BatchState* st, int forced) {
   if (!forced && *(volatile const int*)&st->halt) return;
   for (int t = blockIdx.x; t < bd.ntiles; t += gridDim.x) {
@@ -307,18 +319,19 @@ __global__ void batch_xpay_kernel(BatchDesc bd, SpinorRef r, SpinorRef p, const 
     const int e = sd.off + e_loc;
     const float beta = (float)st->beta[sd.col + e_loc % sd.R];
     cplx<float> rv[12], pv[12];
-    load_spinor<SStore::F32, float>(r, bd.total, e, rv);
-    load_spinor<SStore::F32, float, false>(p, bd.total, e, pv);
+    load_spinor<S, float>(r, bd.total, e, rv);
+    load_spinor<S, float, false>(p, bd.total, e, pv);
 #pragma unroll
     for (int q = 0; q < 12; ++q) {
       pv[q].re = fmaf(beta, pv[q].re, rv[q].re);
       pv[q].im = fmaf(beta, pv[q].im, rv[q].im);
     }
-    store_spinor<SStore::F32, float>(p, bd.total, e, pv);
+    store_spinor<S, float>(p, bd.total, e, pv);
   }
 }
 
 // Start: phi (canonical, per system) -> phi64; x64 = 0; x_lo = 0; r_lo = p_lo = phi; phi2 per column.
+template <SStore S>
 __global__ void batch_init_kernel(BatchDesc bd, SpinorRef phi64, SpinorRef x64, SpinorRef xlo, SpinorRef rlo,
                                   SpinorRef plo, BatchState* st, BatchReduce br) {
   extern __shared__ double smem[];
@@ -345,16 +358,16 @@ __global__ void batch_init_kernel(BatchDesc bd, SpinorRef phi64, SpinorRef x64, 
       }
       store_spinor<SStore::F64, double>(phi64, bd.total, e, a);
       store_spinor<SStore::F64, double>(x64, bd.total, e, z);
-      store_spinor<SStore::F32, double>(xlo, bd.total, e, z);
-      store_spinor<SStore::F32, double>(rlo, bd.total, e, a);
-      store_spinor<SStore::F32, double>(plo, bd.total, e, a);
+      store_spinor<S, double>(xlo, bd.total, e, z);
+      store_spinor<S, double>(rlo, bd.total, e, a);
+      store_spinor<S, double>(plo, bd.total, e, a);
     }
     tile_columns(sd, v, sh_tile, sh_col);
   }
   auto fin = [&](const double* tot) {
     for (int c = 0; c < bd.ncols; ++c) {
       st->phi2[c] = tot[c];
-      st->rr[c] = st->rr_prev[c] = st->rr_true[c] = tot[c];
+      st->rr[c] = st->rr_prev[c] = st->rr_true[c] = st->rr_ref[c] = tot[c];
       st->done[c] = tot[c] == 0.0 ? 1 : 0;
       st->conv_iter[c] = 0;
       st->alpha[c] = st->beta[c] = 0.0;
@@ -365,15 +378,16 @@ __global__ void batch_init_kernel(BatchDesc bd, SpinorRef phi64, SpinorRef x64, 
 }
 
 // x64 += x_lo; x_lo = 0
+template <SStore S>
 __global__ void batch_accumulate_kernel(int total, SpinorRef xlo, SpinorRef x64) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     cplx<double> a[12], b[12], z[12];
-    load_spinor<SStore::F32, double, false>(xlo, total, e, a);
+    load_spinor<S, double, false>(xlo, total, e, a);
     load_spinor<SStore::F64, double, false>(x64, total, e, b);
 #pragma unroll
     for (int q = 0; q < 12; ++q) { b[q] = b[q] + a[q]; z[q] = {0.0, 0.0}; }
     store_spinor<SStore::F64, double>(x64, total, e, b);
-    store_spinor<SStore::F32, double>(xlo, total, e, z);
+    store_spinor<S, double>(xlo, total, e, z);
   }
 }
 
@@ -425,6 +439,7 @@ void free_batch(BatchWork* w) {
   for (auto& g : w->graphs) cudaGraphExecDestroy(g.second);
   for (Field* f : {&w->phi64, &w->x64, &w->r64, &w->tmp64, &w->plo, &w->tlo, &w->rlo, &w->xlo}) {
     if (f->data) cudaFree(f->data);
+    if (f->norm) cudaFree(f->norm);
   }
   if (w->st) cudaFree(w->st);
   if (w->st_host) cudaFreeHost(w->st_host);
@@ -473,25 +488,78 @@ void launch_batch(const BatchDesc& bd, SpinorRef in, const Epi& epi, const Batch
   batch_dslash_kernel<T, G, SI, DAG, Epi><<<grid, bd.tile, sh, st>>>(bd, in, epi, br, use64);
 }
 
-template <GStore G>
+template <GStore G, SStore S>
 void batch_iteration(BatchWork* w, const BatchDesc& bd, cudaStream_t st) {
-  BEpiCG1 e1{w->tlo.ref(), bd.total, w->st};
-  launch_batch<float, G, SStore::F32, false>(bd, w->plo.ref(), e1, w->br, 0, w->grid_cap, st);
-  BEpiCG2 e2{w->rlo.ref(), w->xlo.ref(), w->plo.ref(), bd.total, w->st};
-  launch_batch<float, G, SStore::F32, true>(bd, w->tlo.ref(), e2, w->br, 0, w->grid_cap, st);
-  batch_xpay_kernel<<<std::min(bd.ntiles, w->grid_cap), bd.tile, 0, st>>>(bd, w->rlo.ref(), w->plo.ref(), w->st, 0);
+  BEpiCG1<S> e1{w->tlo.ref(), bd.total, w->st};
+  launch_batch<float, G, S, false>(bd, w->plo.ref(), e1, w->br, 0, w->grid_cap, st);
+  BEpiCG2<S> e2{w->rlo.ref(), w->xlo.ref(), w->plo.ref(), bd.total, w->st};
+  launch_batch<float, G, S, true>(bd, w->tlo.ref(), e2, w->br, 0, w->grid_cap, st);
+  batch_xpay_kernel<S><<<std::min(bd.ntiles, w->grid_cap), bd.tile, 0, st>>>(bd, w->rlo.ref(), w->plo.ref(),
+                                                                             w->st, 0);
 }
 
 void batch_iteration_prec(BatchWork* w, const BatchDesc& bd, int prec, cudaStream_t st) {
-  if (prec == LQ_F32_12) batch_iteration<GStore::F32_12>(w, bd, st);
-  else batch_iteration<GStore::F32_18>(w, bd, st);
+  switch (prec) {
+    case LQ_F32_12: batch_iteration<GStore::F32_12, SStore::F32>(w, bd, st); break;
+    case LQ_F16_12: batch_iteration<GStore::F16_12, SStore::F16>(w, bd, st); break;
+    case LQ_I16_12: batch_iteration<GStore::I16_12, SStore::I16>(w, bd, st); break;
+    default: batch_iteration<GStore::F32_18, SStore::F32>(w, bd, st); break;
+  }
 }
 
-void batch_true_residual(BatchWork* w, const BatchDesc& bd, cudaStream_t st) {
+template <SStore S>
+void batch_true_residual_s(BatchWork* w, const BatchDesc& bd, cudaStream_t st) {
   BEpiStore64 e0{w->tmp64.ref(), bd.total};
   launch_batch<double, GStore::F64_18, SStore::F64, false>(bd, w->x64.ref(), e0, w->br, 1, w->grid_cap, st);
-  BEpiResidual e1{w->phi64.ref(), w->r64.ref(), w->rlo.ref(), bd.total, w->st};
+  BEpiResidual<S> e1{w->phi64.ref(), w->r64.ref(), w->rlo.ref(), bd.total, w->st};
   launch_batch<double, GStore::F64_18, SStore::F64, true>(bd, w->tmp64.ref(), e1, w->br, 1, w->grid_cap, st);
+}
+
+void batch_true_residual(BatchWork* w, const BatchDesc& bd, int prec, cudaStream_t st) {
+  switch (spinor_store_of(prec)) {
+    case SStore::F16: batch_true_residual_s<SStore::F16>(w, bd, st); break;
+    case SStore::I16: batch_true_residual_s<SStore::I16>(w, bd, st); break;
+    default: batch_true_residual_s<SStore::F32>(w, bd, st); break;
+  }
+}
+
+// the format-dependent element kernels of the host loop
+void batch_init(BatchWork* w, const BatchDesc& bd, int prec, int grid, cudaStream_t st) {
+  const size_t sh = sizeof(double) * (bd.tile + bd.ncols);
+  switch (spinor_store_of(prec)) {
+    case SStore::F16:
+      batch_init_kernel<SStore::F16><<<grid, bd.tile, sh, st>>>(bd, w->phi64.ref(), w->x64.ref(), w->xlo.ref(),
+                                                                w->rlo.ref(), w->plo.ref(), w->st, w->br);
+      break;
+    case SStore::I16:
+      batch_init_kernel<SStore::I16><<<grid, bd.tile, sh, st>>>(bd, w->phi64.ref(), w->x64.ref(), w->xlo.ref(),
+                                                                w->rlo.ref(), w->plo.ref(), w->st, w->br);
+      break;
+    default:
+      batch_init_kernel<SStore::F32><<<grid, bd.tile, sh, st>>>(bd, w->phi64.ref(), w->x64.ref(), w->xlo.ref(),
+                                                                w->rlo.ref(), w->plo.ref(), w->st, w->br);
+      break;
+  }
+}
+void batch_reliable_tail(BatchWork* w, const BatchDesc& bd, const BatchDesc& bd64, int prec, int grid,
+                         cudaStream_t st) {
+  switch (spinor_store_of(prec)) {
+    case SStore::F16:
+      batch_accumulate_kernel<SStore::F16><<<grid, bd.tile, 0, st>>>(bd.total, w->xlo.ref(), w->x64.ref());
+      batch_true_residual(w, bd64, prec, st);
+      batch_xpay_kernel<SStore::F16><<<grid, bd.tile, 0, st>>>(bd, w->rlo.ref(), w->plo.ref(), w->st, 1);
+      break;
+    case SStore::I16:
+      batch_accumulate_kernel<SStore::I16><<<grid, bd.tile, 0, st>>>(bd.total, w->xlo.ref(), w->x64.ref());
+      batch_true_residual(w, bd64, prec, st);
+      batch_xpay_kernel<SStore::I16><<<grid, bd.tile, 0, st>>>(bd, w->rlo.ref(), w->plo.ref(), w->st, 1);
+      break;
+    default:
+      batch_accumulate_kernel<SStore::F32><<<grid, bd.tile, 0, st>>>(bd.total, w->xlo.ref(), w->x64.ref());
+      batch_true_residual(w, bd64, prec, st);
+      batch_xpay_kernel<SStore::F32><<<grid, bd.tile, 0, st>>>(bd, w->rlo.ref(), w->plo.ref(), w->st, 1);
+      break;
+  }
 }
 
 }  // namespace
@@ -512,7 +580,8 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
   if (!x || !phi || !kappa) return fail(LQ_ERR_ARG, "null argument");
   if (nrhs <= 0 || nrhs > 16 || n * nrhs > kMaxCols) return fail(LQ_ERR_ARG, "need 1 <= nrhs <= 16, n * nrhs <= 64");
   if (!(tol > 0.0) || maxiter <= 0 || reliable_every <= 0) return fail(LQ_ERR_ARG, "bad tol, maxiter or reliable_every");
-  if (inner_prec != LQ_F32 && inner_prec != LQ_F32_12) return fail(LQ_ERR_ARG, "inner precision must be LQ_F32 or LQ_F32_12");
+  if (inner_prec != LQ_F32 && inner_prec != LQ_F32_12 && inner_prec != LQ_F16_12 && inner_prec != LQ_I16_12)
+    return fail(LQ_ERR_ARG, "inner precision must be LQ_F32, LQ_F32_12, LQ_F16_12 or LQ_I16_12");
   for (int k = 0; k < n; ++k) {
     if (!ctxs[k] || !ctxs[k]->gauge_set) return fail(LQ_ERR_STATE, "every context needs a gauge field");
     if (ctxs[k]->device != c->device) return fail(LQ_ERR_ARG, "all contexts must be on one device");
@@ -556,9 +625,11 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
     auto alloc = [&](Field& f, SStore s) {
       f.store = s;
       ok = ok && cudaMalloc(&f.data, spinor_bytes(s, w->total)) == cudaSuccess;
+      if (s == SStore::F16 || s == SStore::I16) ok = ok && cudaMalloc(&f.norm, sizeof(float) * w->total) == cudaSuccess;
     };
+    const SStore slo = spinor_store_of(inner_prec);
     alloc(w->phi64, SStore::F64); alloc(w->x64, SStore::F64); alloc(w->r64, SStore::F64); alloc(w->tmp64, SStore::F64);
-    alloc(w->plo, SStore::F32); alloc(w->tlo, SStore::F32); alloc(w->rlo, SStore::F32); alloc(w->xlo, SStore::F32);
+    alloc(w->plo, slo); alloc(w->tlo, slo); alloc(w->rlo, slo); alloc(w->xlo, slo);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     w->grid_cap = std::max(1, sms) * 4;
@@ -585,6 +656,7 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
   // state
   BatchState h{};
   h.stop2 = tol * tol;
+  h.delta2 = inner_prec == LQ_F32 || inner_prec == LQ_F32_12 ? 1e-6 : 1e-4;
   h.ru_every = reliable_every;
   h.maxiter = maxiter;
   h.hist = (hist && hist_len > 0) ? w->hist : nullptr;
@@ -603,8 +675,7 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
       if (t <= 256 && std::find(cand.begin(), cand.end(), t) == cand.end()) cand.push_back(t);
     }
     BatchDesc bd0 = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, cand[0]);
-    batch_init_kernel<<<std::min(bd0.ntiles, w->grid_cap), bd0.tile, sizeof(double) * (bd0.tile + bd0.ncols), st>>>(
-        bd0, w->phi64.ref(), w->x64.ref(), w->xlo.ref(), w->rlo.ref(), w->plo.ref(), w->st, w->br);
+    batch_init(w, bd0, inner_prec, std::min(bd0.ntiles, w->grid_cap), st);
     float best = 1e30f;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
@@ -630,8 +701,7 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
   // FP64 passes (~140 registers per thread) use tiles of about 128 threads
   const BatchDesc bd64 = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, std::max(nrhs, 128 / nrhs * nrhs));
   const int grid = std::min(bd.ntiles, w->grid_cap);
-  batch_init_kernel<<<grid, bd.tile, sizeof(double) * (bd.tile + bd.ncols), st>>>(
-      bd, w->phi64.ref(), w->x64.ref(), w->xlo.ref(), w->rlo.ref(), w->plo.ref(), w->st, w->br);
+  batch_init(w, bd, inner_prec, grid, st);
   s.kernel_launches += 1;
 
   // iterations as CUDA graphs of reliable_every iterations
@@ -664,9 +734,7 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
     if (err != cudaSuccess) break;
     s.kernel_launches += 3 * chunk;
     // reliable update: fold x, FP64 true residual per column, freeze converged columns
-    batch_accumulate_kernel<<<grid, bd.tile, 0, st>>>(bd.total, w->xlo.ref(), w->x64.ref());
-    batch_true_residual(w, bd64, st);
-    batch_xpay_kernel<<<grid, bd.tile, 0, st>>>(bd, w->rlo.ref(), w->plo.ref(), w->st, 1);
+    batch_reliable_tail(w, bd, bd64, inner_prec, grid, st);
     s.kernel_launches += 4;
     s.reliable_updates++;
     err = cudaMemcpyAsync(w->st_host, w->st, sizeof(BatchState), cudaMemcpyDeviceToHost, st);

@@ -31,7 +31,7 @@ def _true_residuals(lq, dims, U, xs, phis, kappa):
         lq.lq_destroy(ctx)
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 3, 6])
 def test_multi_rhs_matches_oracle(lq, prec):
     dims, R, kappa = (4, 4, 4, 4), 12, 0.155
     lat = Lattice(dims)
@@ -72,7 +72,7 @@ def test_uneven_lattices_one_launch_match_oracle(lq):
             Us.append(U)
             phis.append(dev(source(lat, 4 + k)))
             xs.append(torch.zeros_like(phis[-1]))
-        status, st, iters, resid, _ = lq.lq_solve_batch(ctxs, xs, phis, kappas, 1, 1e-10, 5000, lq.LQ_F32_12, 50)
+        status, st, iters, resid, _ = lq.lq_solve_batch(ctxs, xs, phis, kappas, 1, 1e-10, 5000, lq.LQ_I16_12, 50)
         got = [host(x) for x in xs]
     finally:
         for c in ctxs:
@@ -100,7 +100,9 @@ def test_batch_reuses_workspace_and_rejects_bad_arguments(lq):
         with pytest.raises(lq.LQError):
             lq.lq_solve_batch([ctx], [host(x1)], [phi], [0.15], 2)   # host buffer
         with pytest.raises(lq.LQError):
-            lq.lq_solve_batch([ctx], [x1], [phi], [0.15], 2, inner_prec=lq.LQ_F16_12)
+            lq.lq_solve_batch([ctx], [x1], [phi], [0.15], 2, inner_prec=lq.LQ_BF16_12)
+        with pytest.raises(lq.LQError):
+            lq.lq_solve_batch([ctx], [x1], [phi], [0.15], 2, inner_prec=lq.LQ_DF64)
     finally:
         lq.lq_destroy(ctx)
 
