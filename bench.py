@@ -246,6 +246,38 @@ def measure_extras(lq, torch, dev):
     return out
 
 
+def run_hmc_ensemble(args):
+    """A run of HMC trajectories (no timing contract): 32^4, beta 5.7, kappa 0.155, --md-steps
+    leapfrog steps (25), tau 1, mixed-precision solves, from the exp(iA) start (sigma 0.3, seed 8); prints
+    per-trajectory Delta H, decisions, plaquettes and <exp(-Delta H)>."""
+    import numpy as np
+    import torch
+    import paper_1207_2223_gb300 as lq
+    from synth import Lattice, gauge_exp_iA, momenta, chi_noise, metropolis_uniform
+    dims = tuple(args.dims) if tuple(args.dims) != DIMS else (32, 32, 32, 32)
+    lat = Lattice(dims)
+    ctx = lq.lq_create(dims)
+    lq.lq_gauge_set(ctx, torch.from_numpy(gauge_exp_iA(lat, 0.3, 8)).cuda())
+    rows = []
+    for traj in range(args.steps):
+        p = torch.from_numpy(momenta(lat, 8, traj)).cuda()
+        chi = torch.from_numpy(chi_noise(lat, 8, traj)).cuda()
+        r = lq.lq_hmc_trajectory(ctx, p, chi, metropolis_uniform(8, traj), 5.7, 0.155, args.md_steps, 1.0, 1e-10,
+                                 20000, lq.PRECISIONS[args.inner], 50)
+        rows.append(r)
+        print(json.dumps({"traj": traj, "dH": r["dH"], "accepted": r["accepted"], "plaquette": r["plaquette"],
+                          "seconds": r["seconds"], "cg_iterations": r["cg_iterations"]}), flush=True)
+    lq.lq_destroy(ctx)
+    dh = np.array([r["dH"] for r in rows])
+    e = np.exp(-dh)
+    print(json.dumps({"workload": "hmc_%dx%dx%dx%d" % dims, "md_steps": args.md_steps, "trajectories": len(rows),
+                      "acceptance": float(np.mean([r["accepted"] for r in rows])),
+                      "exp_minus_dH_mean": float(e.mean()), "exp_minus_dH_err": float(e.std() / np.sqrt(len(e))),
+                      "plaquette_last": rows[-1]["plaquette"],
+                      "seconds_per_trajectory": float(np.mean([r["seconds"] for r in rows]))}), flush=True)
+    return 0
+
+
 def run_reference(args):
     import numpy as np
     rank, size = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
@@ -498,11 +530,17 @@ def main():
                          "batched solve of --steps iterations")
     ap.add_argument("--prec", default="f32_12", choices=["f64", "f32", "f32_12", "f16_12", "bf16_12", "i16_12"])
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
+    ap.add_argument("--md-steps", type=int, default=25, help="leapfrog steps per trajectory (--hmc-ensemble)")
+    ap.add_argument("--hmc-ensemble", action="store_true",
+                    help="run --steps HMC trajectories at 32^4 (beta 5.7, kappa 0.155, 25 steps) and report "
+                         "acceptance and <exp(-dH)> instead of the benchmark")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.kernel_only:
         return run_kernel_only(args)
+    if args.hmc_ensemble:
+        return run_hmc_ensemble(args)
     return run_ours(args)
 
 

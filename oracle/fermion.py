@@ -29,23 +29,27 @@ def pseudofermion_action(U, phi, dims, kappa, tol=1e-10, t_antiperiodic=True):
     return float(np.vdot(phi, X).real)
 
 
-def fermion_force_from_X(U, X, dims, kappa, t_antiperiodic=True):
-    """F_a(x, mu), shape (V, 4, 8), given X = (M^dag M)^{-1} phi."""
-    fwd, _, sf, _ = neighbours(dims, t_antiperiodic)
-    Y = apply_M(U, X, dims, kappa, t_antiperiodic)
-    F = np.zeros(U.shape[:2] + (8,))
+def fermion_force_from_X(U, X, dims, kappa, t_antiperiodic=True, sites=None):
+    """F_a(x, mu) at ``sites`` (all sites when None), shape (n, 4, 8), given X = (M^dag M)^{-1} phi."""
+    nbr = neighbours(dims, t_antiperiodic)
+    fwd, _, sf, _ = nbr
+    x = np.arange(U.shape[0]) if sites is None else np.asarray(sites)
+    F = np.zeros((len(x), 4, 8))
+    # Y = M X, needed at x and at x + mu only
+    Y = apply_M(U, X, dims, kappa, t_antiperiodic, sites=x, nbr=nbr)
     for mu in range(4):
-        s = sf[mu][:, None]
-        Xf = X[fwd[mu]]
-        Yf = Y[fwd[mu]]
-        Um = U[:, mu]
+        s = sf[mu][x][:, None]
+        xf = fwd[mu][x]
+        Yf = apply_M(U, X, dims, kappa, t_antiperiodic, sites=xf, nbr=nbr)
+        Xf = X[xf]
+        Um = U[x, mu]
         Yp = np.matmul(ONE4 - GAMMA[mu], Y)            # (1 - g_mu) Y(x)
         Ym = np.matmul(ONE4 + GAMMA[mu], Yf)           # (1 + g_mu) Y(x+mu)
         UXf = np.matmul(Xf, np.swapaxes(Um, -1, -2))   # U X(x+mu), spin-major
         # term 1: Y(x)^dag (1-g) t_a U X(x+mu) = sum_{s,i,j} conj(Yp[s,i]) t_a[i,j] (U Xf)[s,j]
         t1 = np.einsum("vsi,aij,vsj->va", np.conj(Yp), T, UXf)
         # term 2: Y(x+mu)^dag (1+g) U^dag t_a X(x) = sum conj(Ym[s,i]) conj(U[j,i]) t_a[j,k] X[s,k]
-        t2 = np.einsum("vsi,vji,ajk,vsk->va", np.conj(Ym), np.conj(Um), T, X)
+        t2 = np.einsum("vsi,vji,ajk,vsk->va", np.conj(Ym), np.conj(Um), T, X[x])
         F[:, mu] = 2.0 * kappa * s * (1j * t1 - 1j * t2).real
     return F
 

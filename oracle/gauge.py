@@ -37,23 +37,26 @@ def gauge_action(U, dims, beta):
     return float(beta * np.sum(1.0 - plaquette_field(U, dims) / 3.0))
 
 
-def staple_sum(U, dims):
-    """Sigma_mu(x), shape (V, 4, 3, 3)."""
+def staple_sum(U, dims, sites=None):
+    """Sigma_mu(x) at ``sites`` (all sites when None), shape (n, 4, 3, 3)."""
     fwd, bwd, _, _ = neighbours(dims, False)
-    S = np.zeros_like(U)
+    x = np.arange(U.shape[0]) if sites is None else np.asarray(sites)
+    S = np.zeros((len(x), 4, 3, 3), dtype=np.complex128)
     for mu in range(4):
         for nu in range(4):
             if nu == mu:
                 continue
-            upper = U[fwd[mu], nu] @ dagger(U[fwd[nu], mu]) @ dagger(U[:, nu])
-            xmn = bwd[nu][fwd[mu]]                   # x + mu - nu
-            lower = dagger(U[xmn, nu]) @ dagger(U[bwd[nu], mu]) @ U[bwd[nu], nu]
+            xm, xn, xb = fwd[mu][x], fwd[nu][x], bwd[nu][x]
+            upper = U[xm, nu] @ dagger(U[xn, mu]) @ dagger(U[x, nu])
+            xmn = bwd[nu][xm]                        # x + mu - nu
+            lower = dagger(U[xmn, nu]) @ dagger(U[xb, mu]) @ U[xb, nu]
             S[:, mu] += upper + lower
     return S
 
 
-def gauge_force(U, dims, beta):
-    """F_a(x, mu) = (beta/3) Im tr(t_a U_mu(x) Sigma_mu(x)), shape (V, 4, 8)."""
-    W = U @ staple_sum(U, dims)
+def gauge_force(U, dims, beta, sites=None):
+    """F_a(x, mu) = (beta/3) Im tr(t_a U_mu(x) Sigma_mu(x)) at ``sites``, shape (n, 4, 8)."""
+    x = np.arange(U.shape[0]) if sites is None else np.asarray(sites)
+    W = U[x] @ staple_sum(U, dims, sites)
     tr = np.einsum("aij,...ji->...a", T, W)
     return (beta / 3.0) * tr.imag

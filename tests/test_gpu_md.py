@@ -76,6 +76,28 @@ def test_fermion_force(lq, dims, antiperiodic):
     assert np.max(np.abs(F - ref)) < 1e-12 * np.max(np.abs(ref))
 
 
+def test_forces_full_size_sampled_links(lq):
+    """32^4 (the HMC lattice of the differentiable-action workload): gauge and fermion force at
+    sampled links against the oracle evaluated link by link."""
+    dims = (32, 32, 32, 32)
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, 0.3, 8)
+    X = source(lat, 9)
+    rng = np.random.default_rng(3)
+    sites = np.unique(np.concatenate([rng.integers(0, lat.V, 150), [0, lat.V - 1, 32 ** 3 * 31 + 5]]))
+    ctx = _ctx(lq, dims, U)
+    try:
+        F = torch.empty((lat.V, 4, 8), dtype=torch.float64, device="cuda")
+        lq.lq_gauge_force(ctx, F, 5.7)
+        Fg = host(F)[sites]
+        lq.lq_fermion_force(ctx, F, dev(X), 0.155)
+        Ff = host(F)[sites]
+    finally:
+        lq.lq_destroy(ctx)
+    assert rel_err(Fg, gauge_force(U, dims, 5.7, sites=sites)) < 1e-12
+    assert rel_err(Ff, fermion_force_from_X(U, X, dims, 0.155, sites=sites)) < 1e-12
+
+
 @pytest.mark.parametrize("eps", [0.1, 1.3])
 def test_link_update(lq, eps):
     dims = (4, 2, 4, 6)
@@ -162,3 +184,24 @@ def test_trajectory_reject_restores_links(lq):
     assert abs(r["dH"] - ref["dH"]) < 1e-9
     assert np.array_equal(Ug, U)
     assert r["plaquette"] == pytest.approx(plaquette(U, dims), abs=1e-13)
+
+
+def test_full_size_trajectory_delta_H_scales_as_eps_squared(lq):
+    """24^4 (beta 5.6, kappa 0.155, sigma 0.3 reunitarised start, tau 1): a property that holds at
+    any size and that the oracle cannot reach at this volume: Delta H falls as eps^2 once the
+    leapfrog is inside its stability region (80 -> 160 steps: ratio 4)."""
+    dims = (24, 24, 24, 24)
+    lat = Lattice(dims)
+    U = dev(gauge_exp_iA(lat, 0.3, 1, reunitarise=True))
+    p0 = dev(momenta(lat, 1))
+    chi = dev(chi_noise(lat, 1))
+    dh = []
+    for n in (80, 160):
+        ctx = lq.lq_create(dims)
+        try:
+            lq.lq_gauge_set(ctx, U)
+            r = lq.lq_hmc_trajectory(ctx, p0.clone(), chi, 0.5, 5.6, 0.155, n, 1.0, 1e-10, 20000, lq.LQ_I16_12, 50)
+        finally:
+            lq.lq_destroy(ctx)
+        dh.append(r["dH"])
+    assert 3.8 < dh[0] / dh[1] < 4.2, dh

@@ -77,6 +77,24 @@ def test_mixed_solve_with_and_without_double_float_updates(lq, df_updates):
     assert st["reliable_updates"] >= 2
 
 
+def test_kappa_zero_is_identity(lq):
+    """kappa = 0: M = 1, so M^dag M x = phi gives x = phi in one iteration."""
+    dims = (4, 2, 2, 6)
+    lat = Lattice(dims)
+    phi = source(lat, 4)
+    ctx = lq.lq_create(dims)
+    try:
+        lq.lq_gauge_set(ctx, dev(gauge_exp_iA(lat, 0.3, 4)))
+        for prec in (lq.LQ_F64, lq.LQ_I16_12):
+            x = torch.zeros_like(dev(phi))
+            status, st = lq.lq_solve_MdagM(ctx, x, dev(phi), 0.0, 1e-10, 100, prec, 50)
+            # FP64: one iteration; 16-bit storage: a few, each removing the rounding of the last
+            assert status == lq.LQ_OK and st["iterations"] <= (1 if prec == lq.LQ_F64 else 8)
+            assert rel_err(host(x), phi) < 1e-10
+    finally:
+        lq.lq_destroy(ctx)
+
+
 def test_zero_source_and_errors(lq):
     dims = (4, 4, 4, 4)
     lat = Lattice(dims)

@@ -174,3 +174,16 @@ def test_fermion_force_gauge_covariant():
     F = fermion_force_from_X(U, X, dims, 0.15)
     Fg = fermion_force_from_X(Ug, Xg, dims, 0.15)
     assert np.max(np.abs(np.sum(F ** 2, -1) - np.sum(Fg ** 2, -1))) < 1e-12
+
+
+def test_forces_at_sampled_sites_equal_full_evaluation():
+    """The site-sampled evaluation used for full-size parity equals the full one."""
+    dims = (4, 2, 4, 6)
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, 0.4, 21)
+    X = source(lat, 21)
+    sites = np.array([0, 7, 19, 33, lat.V - 1, 100])
+    assert np.array_equal(gauge_force(U, dims, 5.6, sites=sites), gauge_force(U, dims, 5.6)[sites])
+    full = fermion_force_from_X(U, X, dims, 0.15)
+    part = fermion_force_from_X(U, X, dims, 0.15, sites=sites)
+    assert np.max(np.abs(part - full[sites])) < 1e-14
