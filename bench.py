@@ -57,9 +57,9 @@ DSLASH_FLOPS = 1368
 # hash; see profiles/.  Null when the kernel changed since the capture.
 NCU_TRAFFIC = {
     # profiles/cg_pass2_i16_12_32x32x32x32.md
-    "i16_12": {"bytes_per_site": 384.2, "src": "2a3cbf4942624785"},
+    "i16_12": {"bytes_per_site": 384.3, "src": "65325eff0bb07804"},
     # profiles/cg_pass2_f32_12_32x32x32x32.md
-    "f32_12": {"bytes_per_site": 754.9, "src": "2a3cbf4942624785"},
+    "f32_12": {"bytes_per_site": 755.4, "src": "65325eff0bb07804"},
 }
 
 
@@ -314,6 +314,7 @@ def run_kernel_only(args):
     lat = Lattice(dims)
     U, phi = gauge_exp_iA(lat, SIGMA, SEED), source(lat, SEED)
     ctx = lq.lq_create(dims)
+    lq.lq_set_option(ctx, lq.LQ_OPT_PAIR_SITES, args.pair_sites)
     lq.lq_gauge_set(ctx, torch.from_numpy(U).cuda())
     p = torch.from_numpy(phi).cuda()
     prec = lq.PRECISIONS[args.prec]
@@ -434,6 +435,21 @@ def run_ours(args):
             cg[which] = {"ms": round(ms, 5), "GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4),
                          "bytes_per_site": CG_BYTES[args.inner][which]}
         cg["iteration_ms"] = round(lq.lq_time_cg_kernel(ctx, phid, KAPPA, 0, inner, 40), 5)
+        # the two-site packed FP32x2 variant of the 16-bit passes (LQ_OPT_PAIR_SITES, off by
+        # default: fewer instructions, same FMA-pipe time, lower occupancy)
+        two_site = None
+        if args.inner == "i16_12":
+            lq.lq_set_option(ctx, lq.LQ_OPT_PAIR_SITES, 1)
+            two_site = {w: round(lq.lq_time_cg_kernel(ctx, phid, KAPPA, int(w[1]), inner, 40), 5)
+                        for w in ("k1", "k2")}
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            sto = solve(inner)
+            q1.record(stream)
+            torch.cuda.synchronize(dev)
+            two_site["solve_s"] = q0.elapsed_time(q1) / 1e3
+            two_site["iterations"] = sto["iterations"]
+            lq.lq_set_option(ctx, lq.LQ_OPT_PAIR_SITES, 0)
         src_hash = kernel_source_hash()
         tr = NCU_TRAFFIC.get(args.inner)
         traffic = tr["bytes_per_site"] * V if tr and tr.get("src") == src_hash else None
@@ -503,7 +519,8 @@ def run_ours(args):
             "iterations": {"mixed": stats[-1]["iterations"], "reliable_updates": stats[-1]["reliable_updates"],
                            "fp64": st64["iterations"]},
             "true_rel_resid": {"mixed": stats[-1]["true_rel_resid"], "fp64": st64["true_rel_resid"]},
-            "roofline": roofline, "cg_kernels": cg, "dslash": dsl, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+            "roofline": roofline, "cg_kernels": cg, "cg_kernels_two_site": two_site, "dslash": dsl, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if extras is not None:
@@ -531,6 +548,8 @@ def main():
     ap.add_argument("--prec", default="f32_12", choices=["f64", "f32", "f32_12", "f16_12", "bf16_12", "i16_12"])
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
     ap.add_argument("--md-steps", type=int, default=25, help="leapfrog steps per trajectory (--hmc-ensemble)")
+    ap.add_argument("--pair-sites", type=int, default=0, choices=[0, 1],
+                    help="--kernel-only: two-site packed stencil for i16_12 (LQ_OPT_PAIR_SITES)")
     ap.add_argument("--hmc-ensemble", action="store_true",
                     help="run --steps HMC trajectories at 32^4 (beta 5.7, kappa 0.155, 25 steps) and report "
                          "acceptance and <exp(-dH)> instead of the benchmark")

@@ -120,8 +120,14 @@ lq_status lq_set_stream(lq_ctx* ctx, void* cuda_stream);
  *                       FP64; 1: the intermediate ones in double-float arithmetic (LQ_DF64)
  *                       on the FP32 pipe, the final residual certified in FP64.  (On this
  *                       part the double-float operator is only ~1.3x faster than FP64, so
- *                       the extra certification pass makes option 1 slower overall.) */
-enum { LQ_OPT_CUDA_GRAPHS = 1, LQ_OPT_DF64_UPDATES = 2 };
+ *                       the extra certification pass makes option 1 slower overall.)
+ *   LQ_OPT_PAIR_SITES   0 (default): one site per thread; 1: with LQ_I16_12 and an even
+ *                       L_t, the operator and the CG passes apply the stencil at two sites
+ *                       per thread (x and x + L_t/2 in time) with packed FP32x2 arithmetic.
+ *                       Same operator, results differ only by FP32 rounding.  (On this part
+ *                       option 1 issues 35% fewer instructions but is slower: a packed FMA
+ *                       holds the FMA pipe for two cycles and the occupancy halves.) */
+enum { LQ_OPT_CUDA_GRAPHS = 1, LQ_OPT_DF64_UPDATES = 2, LQ_OPT_PAIR_SITES = 3 };
 lq_status lq_set_option(lq_ctx* ctx, int option, int value);
 
 /* Number of lattice sites V. */

@@ -140,7 +140,7 @@ lq_status run_chunk(lq_ctx* c, int inner, int n, double kappa) {
     LQ_CUDA(c, cudaGetLastError());
     return LQ_OK;
   }
-  auto key = std::make_tuple(0, inner, n, kappa);
+  auto key = std::make_tuple(c->pair_sites, inner, n, kappa);
   auto it = c->graphs.find(key);
   if (it == c->graphs.end()) {
     cudaGraph_t graph = nullptr;
@@ -544,6 +544,7 @@ lq_status lq_set_option(lq_ctx* c, int option, int value) {
   switch (option) {
     case LQ_OPT_CUDA_GRAPHS: c->use_graphs = value ? 1 : 0; return LQ_OK;
     case LQ_OPT_DF64_UPDATES: c->df_updates = value ? 1 : 0; return LQ_OK;
+    case LQ_OPT_PAIR_SITES: c->pair_sites = value ? 1 : 0; return LQ_OK;
     default: return fail(c, LQ_ERR_ARG, "unknown option");
   }
 }
@@ -600,7 +601,7 @@ lq_status lq_apply_M(lq_ctx* c, double* out, const double* in, double kappa, int
   LQ_TRY(stage_spinor_in(c, in, &din));
   launch_pack_spinor(c->geo, din, s, fin.ref(), c->stream);
   const void* gauge = prec == LQ_F64 ? c->gauge64 : c->gauge_lo[prec];
-  apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream);
+  apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites);
   LQ_CUDA(c, cudaGetLastError());
   return deliver_spinor(c, fout, out);
 }
@@ -621,8 +622,8 @@ lq_status lq_apply_MdagM(lq_ctx* c, double* out, const double* in, double kappa,
   LQ_TRY(stage_spinor_in(c, in, &din));
   launch_pack_spinor(c->geo, din, s, fin.ref(), c->stream);
   const void* gauge = prec == LQ_F64 ? c->gauge64 : c->gauge_lo[prec];
-  apply_M_prec(c->geo, prec, gauge, fin.ref(), fmid.ref(), kappa, false, c->stream);
-  apply_M_prec(c->geo, prec, gauge, fmid.ref(), fout.ref(), kappa, true, c->stream);
+  apply_M_prec(c->geo, prec, gauge, fin.ref(), fmid.ref(), kappa, false, c->stream, c->pair_sites);
+  apply_M_prec(c->geo, prec, gauge, fmid.ref(), fout.ref(), kappa, true, c->stream, c->pair_sites);
   LQ_CUDA(c, cudaGetLastError());
   return deliver_spinor(c, fout, out);
 }
@@ -682,14 +683,14 @@ lq_status lq_time_dslash(lq_ctx* c, const double* in, double kappa, int dagger, 
   cudaEvent_t e0, e1;
   LQ_CUDA(c, cudaEventCreate(&e0));
   LQ_CUDA(c, cudaEventCreate(&e1));
-  apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream);   // warm-up
+  apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites);   // warm-up
   double total = 0.0;
   lq_status st = LQ_OK;
   if (flush_l2) {
     for (int i = 0; i < n && st == LQ_OK; ++i) {
       cudaMemsetAsync(flush, i & 0xff, flush_bytes, c->stream);
       cudaEventRecord(e0, c->stream);
-      apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream);
+      apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites);
       cudaEventRecord(e1, c->stream);
       st = cuda_check(c, cudaEventSynchronize(e1), "cudaEventSynchronize");
       float t = 0.f;
@@ -699,7 +700,7 @@ lq_status lq_time_dslash(lq_ctx* c, const double* in, double kappa, int dagger, 
   } else {
     cudaEventRecord(e0, c->stream);
     for (int i = 0; i < n; ++i)
-      apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream);
+      apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites);
     cudaEventRecord(e1, c->stream);
     st = cuda_check(c, cudaEventSynchronize(e1), "cudaEventSynchronize");
     float t = 0.f;

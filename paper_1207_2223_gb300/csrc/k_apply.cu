@@ -14,7 +14,11 @@ static void apply_one(const Geom& g, const void* gauge, SpinorRef in, SpinorRef 
 }
 
 void apply_M_prec(const Geom& g, int prec, const void* gauge, SpinorRef in, SpinorRef out, double kappa,
-                  bool dagger, cudaStream_t stream) {
+                  bool dagger, cudaStream_t stream, bool pair) {
+  if (pair && prec == LQ_I16_12 && pair_geometry(g)) {
+    pair_apply(g, gauge, in, out, kappa, dagger, stream);
+    return;
+  }
   switch (prec) {
     case LQ_F64: apply_one<double, GStore::F64_18, SStore::F64>(g, gauge, in, out, kappa, dagger, stream); break;
     case LQ_F32: apply_one<float, GStore::F32_18, SStore::F32>(g, gauge, in, out, kappa, dagger, stream); break;

@@ -32,8 +32,19 @@ static void step(lq_ctx* c, const void* gauge, int which, double kappa, cudaStre
   }
 }
 
+// The two-site packed passes replace the one-site ones for 16-bit fixed point
+// (the same fields, formats and solver state).
+static bool use_pair(const lq_ctx* c, int prec) {
+  return prec == LQ_I16_12 && c->pair_sites && pair_geometry(c->geo);
+}
+
 void cglo_step(lq_ctx* c, int prec, int which, double kappa, cudaStream_t stream) {
   const void* gauge = c->gauge_lo[prec];
+  if (use_pair(c, prec)) {
+    if (which == 1) pair_cg1(c, gauge, kappa, stream);
+    else pair_cg2(c, gauge, kappa, stream);
+    return;
+  }
   switch (prec) {
     case LQ_F32: step<GStore::F32_18, SStore::F32>(c, gauge, which, kappa, stream); break;
     case LQ_F32_12: step<GStore::F32_12, SStore::F32>(c, gauge, which, kappa, stream); break;
@@ -46,6 +57,13 @@ void cglo_step(lq_ctx* c, int prec, int which, double kappa, cudaStream_t stream
 
 void cglo_iteration(lq_ctx* c, int prec, double kappa, cudaStream_t stream) {
   const void* gauge = c->gauge_lo[prec];
+  if (use_pair(c, prec)) {
+    const int k = (int)SStore::I16;
+    pair_cg1(c, gauge, kappa, stream);
+    pair_cg2(c, gauge, kappa, stream);
+    launch_xpay_p(c->geo, SStore::I16, c->r_lo[k].ref(), c->p_lo[k].ref(), c->state, false, stream);
+    return;
+  }
   switch (prec) {
     case LQ_F32: iteration<GStore::F32_18, SStore::F32>(c, gauge, kappa, stream); break;
     case LQ_F32_12: iteration<GStore::F32_12, SStore::F32>(c, gauge, kappa, stream); break;

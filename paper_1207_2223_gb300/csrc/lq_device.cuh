@@ -350,6 +350,27 @@ __device__ __forceinline__ void load_link(const GaugeRef& g, int V, int mu, int 
   }
 }
 
+// A 16-bit fixed-point link with every row carrying 32767 U: rows 0, 1 are the
+// stored integers and the rebuilt row 2 (32767^2 U) is divided by 32767 once.
+// The stencil folds the remaining 1/32767 into the scale of the half spinor,
+// which it multiplies anyway, instead of scaling the 12 stored reals.
+template <typename T>
+__device__ __forceinline__ void load_link_q16(const GaugeRef& g, int V, int mu, int s, cplx<T> u[9]) {
+  const uint2* p = static_cast<const uint2*>(g.p) + (size_t)mu * 3 * V;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    uint2 w = __ldg(p + (size_t)k * V + s);
+    float2 a = q16_to2(w.x), b = q16_to2(w.y);
+    u[2 * k] = {(T)a.x, (T)a.y}; u[2 * k + 1] = {(T)b.x, (T)b.y};
+  }
+  reconstruct_row2(u);
+#pragma unroll
+  for (int c = 6; c < 9; ++c) {
+    const float2 r = __fmul2_rn(make_float2((float)u[c].re, (float)u[c].im), make_float2(kQ16Inv, kQ16Inv));
+    u[c] = {(T)r.x, (T)r.y};
+  }
+}
+
 // ----------------------------------------------------- spin projection
 // Projector (1 + S gamma_mu) in the DeGrand-Rossi basis.  The projected
 // spinor has rank 2: components 0, 1 ("h0", "h1") determine 2, 3.

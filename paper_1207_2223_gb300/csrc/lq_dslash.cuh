@@ -79,12 +79,15 @@ __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, cons
     cplx<T> h0[3], h1[3];
     project<MU, SF>(p, h0, h1);
     if (MU == 3 && geo.antiperiodic && c[3] == geo.L[3] - 1) sc = -sc;
-    if (SI == SStore::F16 || SI == SStore::BF16 || SI == SStore::I16 || (MU == 3 && geo.antiperiodic)) {
+    if constexpr (G == GStore::I16_12) sc = sc * (T)kQ16Inv;   // links as raw integers
+    if (SI == SStore::F16 || SI == SStore::BF16 || SI == SStore::I16 || G == GStore::I16_12 ||
+        (MU == 3 && geo.antiperiodic)) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) { h0[k] = scale_c(sc, h0[k]); h1[k] = scale_c(sc, h1[k]); }
     }
     cplx<T> u[9];
-    load_link<G, T>(U, geo.V, MU, s, u);
+    if constexpr (G == GStore::I16_12) load_link_q16<T>(U, geo.V, MU, s, u);
+    else load_link<G, T>(U, geo.V, MU, s, u);
     cplx<T> w0[3], w1[3];
     su3_mul(u, h0, w0);
     su3_mul(u, h1, w1);
@@ -97,12 +100,15 @@ __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, cons
     cplx<T> h0[3], h1[3];
     project<MU, -SF>(p, h0, h1);
     if (MU == 3 && geo.antiperiodic && c[3] == 0) sc = -sc;
-    if (SI == SStore::F16 || SI == SStore::BF16 || SI == SStore::I16 || (MU == 3 && geo.antiperiodic)) {
+    if constexpr (G == GStore::I16_12) sc = sc * (T)kQ16Inv;   // links as raw integers
+    if (SI == SStore::F16 || SI == SStore::BF16 || SI == SStore::I16 || G == GStore::I16_12 ||
+        (MU == 3 && geo.antiperiodic)) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) { h0[k] = scale_c(sc, h0[k]); h1[k] = scale_c(sc, h1[k]); }
     }
     cplx<T> u[9];
-    load_link<G, T>(U, geo.V, MU, n, u);
+    if constexpr (G == GStore::I16_12) load_link_q16<T>(U, geo.V, MU, n, u);
+    else load_link<G, T>(U, geo.V, MU, n, u);
     cplx<T> w0[3], w1[3];
     su3_dagmul(u, h0, w0);
     su3_dagmul(u, h1, w1);

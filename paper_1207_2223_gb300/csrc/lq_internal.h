@@ -100,6 +100,7 @@ struct lq_ctx {
   void* batch = nullptr;                 // workspace of lq_solve_batch (k_batch.cu)
   int use_graphs = 1;                    // CG iterations as CUDA graphs (lq_set_option)
   int df_updates = 0;                    // double-float intermediate reliable updates (lq_set_option)
+  int pair_sites = 0;                    // two-site packed stencil for 16-bit storage (lq_set_option)
 };
 
 namespace lq {
@@ -138,8 +139,17 @@ void launch_inner_restart(const Geom& g, SpinorRef src64, SStore s, SpinorRef x,
                           cudaStream_t stream);
 
 // ---- Wilson operator applications (k_apply.cu): out = M in or M^dag in
+// (pair: the two-site packed stencil where it applies, 16-bit fixed point)
 void apply_M_prec(const Geom& g, int prec, const void* gauge, SpinorRef in, SpinorRef out, double kappa,
-                  bool dagger, cudaStream_t stream);
+                  bool dagger, cudaStream_t stream, bool pair = false);
+
+// ---- two-site packed stencil for 16-bit fixed-point storage (k_pair.cu);
+// it pairs x with x + L_t/2 in time, so it needs an even L_t
+inline bool pair_geometry(const Geom& g) { return g.L[3] % 2 == 0; }
+void pair_apply(const Geom& g, const void* gauge, SpinorRef in, SpinorRef out, double kappa, bool dagger,
+                cudaStream_t stream);
+void pair_cg1(lq_ctx* c, const void* gauge, double kappa, cudaStream_t stream);   // t = M p, |t|^2
+void pair_cg2(lq_ctx* c, const void* gauge, double kappa, cudaStream_t stream);   // r -= alpha M^dag t, x += alpha p
 
 // ---- FP64 CG pieces (k_cg64.cu)
 void cg64_iteration(lq_ctx* c, double kappa, cudaStream_t stream);

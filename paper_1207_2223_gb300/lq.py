@@ -159,7 +159,7 @@ def lq_set_stream(ctx, stream):
     _check(ctx, load().lq_set_stream(ctx, stream))
 
 
-LQ_OPT_CUDA_GRAPHS, LQ_OPT_DF64_UPDATES = 1, 2
+LQ_OPT_CUDA_GRAPHS, LQ_OPT_DF64_UPDATES, LQ_OPT_PAIR_SITES = 1, 2, 3
 
 
 def lq_set_option(ctx, option, value):
