@@ -468,14 +468,23 @@ def run_ours(args):
         xh = torch.empty_like(phih).pin_memory()
         lq.lq_gauge_set(ctx, Uh)
         solve(inner, xh, phih)
+        clocks_e2e = Clocks(local)
+        t_set, t_solve = [], []
         t_e = time.perf_counter()
         for _ in range(args.steps):
+            ta = time.perf_counter()
             lq.lq_gauge_set(ctx, Uh)
+            tb = time.perf_counter()
             solve(inner, xh, phih)
+            t_set.append(tb - ta)
+            t_solve.append(time.perf_counter() - tb)
         e2e_local = time.perf_counter() - t_e
+        clk_e2e = clocks_e2e.stop()
         e2e_t, e2e_units = replicas.combine(e2e_local, args.steps, dev)
         e2e = {"value": e2e_units / e2e_t, "unit": "solves/s", "h2d_bytes_per_step": int(U.nbytes + phi.nbytes),
-               "d2h_bytes_per_step": int(phi.nbytes)}
+               "d2h_bytes_per_step": int(phi.nbytes),
+               "gauge_set_ms": round(1e3 * sorted(t_set)[len(t_set) // 2], 2),
+               "solve_ms": round(1e3 * sorted(t_solve)[len(t_solve) // 2], 2), "clocks": clk_e2e}
         # host <-> device copy rate of pinned buffers (context for e2e)
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         c0.record(stream)
