@@ -247,34 +247,54 @@ def measure_extras(lq, torch, dev):
 
 
 def run_hmc_ensemble(args):
-    """A run of HMC trajectories (no timing contract): 32^4, beta 5.7, kappa 0.155, --md-steps
-    leapfrog steps (25), tau 1, mixed-precision solves, from the exp(iA) start (sigma 0.3, seed 8); prints
-    per-trajectory Delta H, decisions, plaquettes and <exp(-Delta H)>."""
+    """A run of HMC trajectories (no timing contract).  Default: 32^4, beta 5.7, kappa 0.155,
+    25 leapfrog steps, tau 1, mixed-precision solves, from the exp(iA) start (sigma 0.3, seed 8).
+    --dims / --beta / --hmc-kappa / --md-steps / --trajectories / --start ordered select other
+    runs (the paper's volume-scaling runs are 200 trajectories from an ordered start).  Prints
+    one line per trajectory and a summary: acceptance, <exp(-Delta H)> and the plaquette over
+    the second half of the run (after thermalisation), time per trajectory and its split."""
     import numpy as np
     import torch
     import paper_1207_2223_gb300 as lq
-    from synth import Lattice, gauge_exp_iA, momenta, chi_noise, metropolis_uniform
+    from synth import Lattice, gauge_exp_iA, identity_gauge, momenta, chi_noise, metropolis_uniform
     dims = tuple(args.dims) if tuple(args.dims) != DIMS else (32, 32, 32, 32)
     lat = Lattice(dims)
     ctx = lq.lq_create(dims)
-    lq.lq_gauge_set(ctx, torch.from_numpy(gauge_exp_iA(lat, 0.3, 8)).cuda())
+    U0 = identity_gauge(lat) if args.start == "ordered" else gauge_exp_iA(lat, 0.3, 8)
+    lq.lq_gauge_set(ctx, torch.from_numpy(U0).cuda())
     rows = []
-    for traj in range(args.steps):
+    t0 = time.perf_counter()
+    for traj in range(args.trajectories):
         p = torch.from_numpy(momenta(lat, 8, traj)).cuda()
         chi = torch.from_numpy(chi_noise(lat, 8, traj)).cuda()
-        r = lq.lq_hmc_trajectory(ctx, p, chi, metropolis_uniform(8, traj), 5.7, 0.155, args.md_steps, 1.0, 1e-10,
-                                 20000, lq.PRECISIONS[args.inner], 50)
+        r = lq.lq_hmc_trajectory(ctx, p, chi, metropolis_uniform(8, traj), args.beta, args.hmc_kappa,
+                                 args.md_steps, 1.0, 1e-10, 20000, lq.PRECISIONS[args.inner], 50)
         rows.append(r)
         print(json.dumps({"traj": traj, "dH": r["dH"], "accepted": r["accepted"], "plaquette": r["plaquette"],
                           "seconds": r["seconds"], "cg_iterations": r["cg_iterations"]}), flush=True)
+    total = time.perf_counter() - t0
     lq.lq_destroy(ctx)
-    dh = np.array([r["dH"] for r in rows])
-    e = np.exp(-dh)
-    print(json.dumps({"workload": "hmc_%dx%dx%dx%d" % dims, "md_steps": args.md_steps, "trajectories": len(rows),
-                      "acceptance": float(np.mean([r["accepted"] for r in rows])),
-                      "exp_minus_dH_mean": float(e.mean()), "exp_minus_dH_err": float(e.std() / np.sqrt(len(e))),
+    half = rows[len(rows) // 2:]
+    e = np.exp(-np.array([r["dH"] for r in half]))
+    plaq = np.array([r["plaquette"] for r in half])
+    dev_t = [r["seconds_solve"] + r["seconds_gauge_force"] + r["seconds_fermion_force"] + r["seconds_link_update"]
+             for r in rows]
+    share = {k: float(np.mean([r["seconds_" + k] / d for r, d in zip(rows, dev_t)]))
+             for k in ("solve", "gauge_force", "fermion_force", "link_update")}
+    print(json.dumps({"workload": "hmc_%dx%dx%dx%d" % dims, "start": args.start, "beta": args.beta,
+                      "kappa": args.hmc_kappa, "md_steps": args.md_steps, "tau": 1.0, "inner": args.inner,
+                      "trajectories": len(rows), "acceptance": float(np.mean([r["accepted"] for r in rows])),
+                      "second_half": {"trajectories": len(half),
+                                      "acceptance": float(np.mean([r["accepted"] for r in half])),
+                                      "exp_minus_dH_mean": float(e.mean()),
+                                      "exp_minus_dH_err": float(e.std() / np.sqrt(len(e))),
+                                      "plaquette_mean": float(plaq.mean()),
+                                      "plaquette_err": float(plaq.std() / np.sqrt(len(plaq)))},
                       "plaquette_last": rows[-1]["plaquette"],
-                      "seconds_per_trajectory": float(np.mean([r["seconds"] for r in rows]))}), flush=True)
+                      "seconds_per_trajectory": float(np.mean([r["seconds"] for r in rows])),
+                      "seconds_total": total,
+                      "cg_iterations_per_trajectory": float(np.mean([r["cg_iterations"] for r in rows])),
+                      "share": share}), flush=True)
     return 0
 
 
@@ -557,6 +577,11 @@ def main():
     ap.add_argument("--prec", default="f32_12", choices=["f64", "f32", "f32_12", "f16_12", "bf16_12", "i16_12"])
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
     ap.add_argument("--md-steps", type=int, default=25, help="leapfrog steps per trajectory (--hmc-ensemble)")
+    ap.add_argument("--trajectories", type=int, default=20, help="--hmc-ensemble: number of trajectories")
+    ap.add_argument("--beta", type=float, default=5.7, help="--hmc-ensemble: gauge coupling")
+    ap.add_argument("--hmc-kappa", type=float, default=0.155, help="--hmc-ensemble: hopping parameter")
+    ap.add_argument("--start", choices=["exp", "ordered"], default="exp",
+                    help="--hmc-ensemble: exp(iA) start (sigma 0.3, seed 8) or ordered start U = 1")
     ap.add_argument("--pair-sites", type=int, default=0, choices=[0, 1],
                     help="--kernel-only: two-site packed stencil for i16_12 (LQ_OPT_PAIR_SITES)")
     ap.add_argument("--hmc-ensemble", action="store_true",
