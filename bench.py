@@ -211,11 +211,19 @@ def measure_extras(lq, torch, dev):
         naive = lq.lq_apply_M_naive(ctx, out_t, phi, KAPPA, False, 3)
         opt64 = lq.lq_time_dslash(ctx, phi, KAPPA, False, lq.LQ_F64, 10, False)
         opt32 = lq.lq_time_dslash(ctx, phi, KAPPA, False, lq.LQ_F32_12, 20, False)
+        del out_t
+        # the force half: naive against optimised fermion-force kernel (X = the source)
+        F = torch.empty((lat.V, 4, 8), dtype=torch.float64, device=dev)
+        naive_f = lq.lq_fermion_force_naive(ctx, F, phi, KAPPA, 3)
+        del F
+        opt_f = lq.lq_time_fermion_force(ctx, phi, KAPPA, 10)
     finally:
         lq.lq_destroy(ctx)
     out["register_ablation_32x32x32x64"] = {"naive_f64_ms": naive, "optimised_f64_ms": opt64,
                                             "optimised_f32_12_ms": opt32, "f64_speedup": naive / opt64,
-                                            "f32_12_speedup": naive / opt32}
+                                            "f32_12_speedup": naive / opt32,
+                                            "naive_fermion_force_ms": naive_f, "optimised_fermion_force_ms": opt_f,
+                                            "fermion_force_speedup": naive_f / opt_f}
     # CG time against iteration count, FP64 CG stopped by the iteration limit (tol 1e-30),
     # with and without CUDA graphs; 8^4 (launch-bound) and 16^4
     for dims in ((8, 8, 8, 8), (16, 16, 16, 16)):

@@ -338,6 +338,21 @@ lq_status lq_time_cg_kernel(lq_ctx* ctx, const double* in, double kappa, int whi
  * its average device time (CUDA events on the context's stream).  Synchronises. */
 lq_status lq_apply_M_naive(lq_ctx* ctx, double* out, const double* in, double kappa, int dagger, int n, double* ms);
 
+/* The force half of the same ablation (Sec. 3 kernel 3 written naively).  F = the fermion
+ * force of lq_fermion_force for the given X, computed with Y = M X from the naive operator
+ * and a naive force kernel: one thread per link, canonical layouts, the neighbour table in
+ * global memory, dense 4x4 spin matrices on full four-spinors, the colour matrix
+ * accumulated in global memory.  F: device, canonical [V][4][8]; X: device, canonical.
+ * When n > 0 and ms != NULL, the force kernel is launched n more times and *ms receives
+ * its average device time.  Synchronises. */
+lq_status lq_fermion_force_naive(lq_ctx* ctx, double* F, const double* X, double kappa, int n, double* ms);
+
+/* Average device time of the optimised fermion-force kernel (Sec. 3 kernel 3, the one
+ * lq_fermion_force and the trajectory use) over n launches, for X (canonical spinor, host
+ * or device) with Y = M X formed once beforehand and not timed.  The context's force
+ * buffer is overwritten.  Synchronises. */
+lq_status lq_time_fermion_force(lq_ctx* ctx, const double* X, double kappa, int n, double* ms);
+
 #ifdef __cplusplus
 }
 #endif

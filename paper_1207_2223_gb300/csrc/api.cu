@@ -948,6 +948,71 @@ lq_status lq_apply_M_naive(lq_ctx* c, double* out, const double* in, double kapp
   return st == LQ_OK ? fin : st;
 }
 
+lq_status lq_fermion_force_naive(lq_ctx* c, double* F, const double* X, double kappa, int n, double* ms) {
+  if (!c) return LQ_ERR_ARG;
+  if (!F || !X || n < 0) return fail(c, LQ_ERR_ARG, "bad buffers or count");
+  if (!is_device_ptr(F) || !is_device_ptr(X) || !aligned16(F) || !aligned16(X))
+    return fail(c, LQ_ERR_ARG, "naive force: device buffers, 16-byte aligned");
+  LQ_TRY(require_gauge(c, LQ_F64));
+  const size_t V = c->geo.V;
+  int* nbr = nullptr;
+  double *sgn = nullptr, *Ucanon = nullptr, *Y = nullptr, *Q = nullptr;
+  LQ_CUDA(c, cudaMallocAsync((void**)&nbr, sizeof(int) * 8 * V, c->stream));
+  LQ_CUDA(c, cudaMallocAsync((void**)&sgn, sizeof(double) * 8 * V, c->stream));
+  LQ_CUDA(c, cudaMallocAsync((void**)&Ucanon, sizeof(double) * 72 * V, c->stream));
+  LQ_CUDA(c, cudaMallocAsync((void**)&Y, sizeof(double) * 24 * V, c->stream));
+  LQ_CUDA(c, cudaMallocAsync((void**)&Q, sizeof(double) * 72 * V, c->stream));
+  naive_setup(c, &nbr, &sgn);
+  launch_unpack_gauge64(c->geo, c->gauge64, Ucanon, c->stream);
+  launch_naive_dslash(c, nbr, sgn, Ucanon, X, Y, kappa, 0);
+  launch_naive_force(c, nbr, sgn, Ucanon, X, Y, Q, F, kappa);
+  lq_status st = cuda_check(c, cudaGetLastError(), "naive force");
+  if (st == LQ_OK && n > 0 && ms) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, c->stream);
+    for (int i = 0; i < n; ++i) launch_naive_force(c, nbr, sgn, Ucanon, X, Y, Q, F, kappa);
+    cudaEventRecord(e1, c->stream);
+    st = cuda_check(c, cudaEventSynchronize(e1), "cudaEventSynchronize");
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    *ms = t / n;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  for (void* p : {(void*)nbr, (void*)sgn, (void*)Ucanon, (void*)Y, (void*)Q}) cudaFreeAsync(p, c->stream);
+  lq_status fin = cuda_check(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  return st == LQ_OK ? fin : st;
+}
+
+lq_status lq_time_fermion_force(lq_ctx* c, const double* X, double kappa, int n, double* ms) {
+  if (!c) return LQ_ERR_ARG;
+  if (!ms || n <= 0) return fail(c, LQ_ERR_ARG, "need n > 0 and ms");
+  LQ_TRY(require_gauge(c, LQ_F64));
+  LQ_TRY(ensure_md_fields(c));
+  const double* dX = nullptr;
+  LQ_TRY(stage_spinor_in(c, X, &dX));
+  launch_pack_spinor(c->geo, dX, SStore::F64, c->x64.ref(), c->stream);
+  apply_M_prec(c->geo, LQ_F64, c->gauge64, c->x64.ref(), c->y64.ref(), kappa, false, c->stream);
+  launch_fermion_force(c->geo, c->gauge64, c->x64.ref(), c->y64.ref(), c->force, kappa, 0.0, false, c->stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, c->stream);
+  for (int i = 0; i < n; ++i)
+    launch_fermion_force(c->geo, c->gauge64, c->x64.ref(), c->y64.ref(), c->force, kappa, 0.0, false, c->stream);
+  cudaEventRecord(e1, c->stream);
+  lq_status st = cuda_check(c, cudaGetLastError(), "fermion force");
+  lq_status sy = cuda_check(c, cudaEventSynchronize(e1), "cudaEventSynchronize");
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  *ms = t / n;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st == LQ_OK ? sy : st;
+}
+
 lq_status lq_time_cg_kernel(lq_ctx* c, const double* in, double kappa, int which, int prec, int n, double* ms) {
   if (!c) return LQ_ERR_ARG;
   if (!ms || n <= 0 || which < 0 || which > 3) return fail(c, LQ_ERR_ARG, "need 0 <= which <= 3, n > 0, ms");

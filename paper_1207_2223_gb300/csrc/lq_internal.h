@@ -109,6 +109,9 @@ namespace lq {
 void naive_setup(lq_ctx* c, int** nbr, double** sgn);
 void launch_naive_dslash(lq_ctx* c, const int* nbr, const double* sgn, const double* Ucanon, const double* in,
                          double* out, double kappa, int dagger);
+// naive fermion force: X, Y canonical, Q scratch [4V][18], F canonical [V][4][8]
+void launch_naive_force(lq_ctx* c, const int* nbr, const double* sgn, const double* Ucanon, const double* X,
+                        const double* Y, double* Q, double* F, double kappa);
 
 // ---- batched solves (k_batch.cu)
 void destroy_batch_work(void* w);

@@ -76,6 +76,8 @@ SIGNATURES = {
     "lq_solve_batch": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_D), _I,
                             _D, _I, _I, _I, _P, _I, _P, _P, ctypes.POINTER(lq_solve_stats)]),
     "lq_apply_M_naive": (_I, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(_D)]),
+    "lq_fermion_force_naive": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_D)]),
+    "lq_time_fermion_force": (_I, [_P, _P, _D, _I, ctypes.POINTER(_D)]),
     "lq_plaquette": (_I, [_P, ctypes.POINTER(_D)]),
     "lq_gauge_action": (_I, [_P, _D, ctypes.POINTER(_D)]),
     "lq_gauge_force": (_I, [_P, _P, _D]),
@@ -240,6 +242,21 @@ def lq_apply_M_naive(ctx, out, inp, kappa, dagger=False, n=0):
     ms = _D(0.0)
     _check(ctx, load().lq_apply_M_naive(ctx, _ptr(out), _ptr(inp), float(kappa), 1 if dagger else 0, int(n),
                                         ctypes.byref(ms)))
+    return ms.value
+
+
+def lq_fermion_force_naive(ctx, F, X, kappa, n=0):
+    """Naive-kernel fermion force (ablation) into F (device, (V, 4, 8)); with n > 0 returns
+    the force kernel's average device ms over n launches."""
+    ms = _D(0.0)
+    _check(ctx, load().lq_fermion_force_naive(ctx, _ptr(F), _ptr(X), float(kappa), int(n), ctypes.byref(ms)))
+    return ms.value
+
+
+def lq_time_fermion_force(ctx, X, kappa, n=20):
+    """Average device ms of the optimised fermion-force kernel (Y = M X formed beforehand)."""
+    ms = _D()
+    _check(ctx, load().lq_time_fermion_force(ctx, _ptr(X), float(kappa), int(n), ctypes.byref(ms)))
     return ms.value
 
 
