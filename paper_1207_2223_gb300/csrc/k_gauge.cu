@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(kBS) gauge_force_kernel(Geom geo, const double
   }
 }
 
-// U_mu(x) <- reunitarise(exp(i eps P) U_mu(x)), P = sum_a p_a t_a
+// U_mu(x) <- reunitarise(exp(i eps P) U_mu(x)), P = sum_a p_a t_a; the exponential by
+// the Cayley-Hamilton closed form (lq_su3.cuh)
 __global__ void __launch_bounds__(kBS) link_update_kernel(Geom geo, double2* g, const double* p, double eps) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= 4 * geo.V) return;
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(kBS) link_update_kernel(Geom geo, double2* g, 
   double pa[8];
 #pragma unroll
   for (int a = 0; a < 8; ++a) pa[a] = p[((size_t)mu * 8 + a) * geo.V + s];
-  const M3 E = expm3(i_eps_algebra(pa, eps));
+  const M3 E = expi_hermitian(eps_algebra(pa, eps));
   M3 U = mul(E, load_m3_rw(g, geo.V, mu, s));
   reunitarise(U);
   store_m3(g, geo.V, mu, s, U);

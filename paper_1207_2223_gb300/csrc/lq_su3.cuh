@@ -101,10 +101,10 @@ __device__ __forceinline__ void im_tr_ta(const M3& W, double f[8]) {
 }
 
 // X = i eps sum_a p_a t_a (anti-Hermitian, traceless)
-__device__ __forceinline__ M3 i_eps_algebra(const double p[8], double eps) {
-  const double r2 = 0.70710678118654752440;
-  const double r6 = 0.40824829046386301637;
-  // P = sum_a p_a t_a (Hermitian)
+// eps P, P = sum_a p_a t_a (Hermitian, traceless)
+__device__ __forceinline__ M3 eps_algebra(const double p[8], double eps) {
+  const double r2 = 0.70710678118654752440 * eps;
+  const double r6 = 0.40824829046386301637 * eps;
   M3 P;
   P.m[0] = {r2 * p[2] + r6 * p[7], 0.0};
   P.m[4] = {-r2 * p[2] + r6 * p[7], 0.0};
@@ -115,9 +115,14 @@ __device__ __forceinline__ M3 i_eps_algebra(const double p[8], double eps) {
   P.m[6] = {r2 * p[3], r2 * p[4]};
   P.m[5] = {r2 * p[5], -r2 * p[6]};
   P.m[7] = {r2 * p[5], r2 * p[6]};
+  return P;
+}
+// i eps P
+__device__ __forceinline__ M3 i_eps_algebra(const double p[8], double eps) {
+  const M3 P = eps_algebra(p, eps);
   M3 X;
 #pragma unroll
-  for (int c = 0; c < 9; ++c) X.m[c] = {-eps * P.m[c].im, eps * P.m[c].re};   // i eps P
+  for (int c = 0; c < 9; ++c) X.m[c] = {-P.m[c].im, P.m[c].re};
   return X;
 }
 
@@ -148,6 +153,65 @@ __device__ __forceinline__ M3 expm3(const M3& X) {
     E.m[0].re += 1.0; E.m[4].re += 1.0; E.m[8].re += 1.0;
   }
   for (int i = 0; i < k; ++i) E = mul(E, E);
+  return E;
+}
+
+// exp(i Q) for Hermitian traceless Q by the Cayley-Hamilton closed form of
+// Morningstar and Peardon, PRD 69 (2004) 054501: exp(iQ) = f0 + f1 Q + f2 Q^2,
+// where the f_j follow from the invariants c0 = det Q = tr(Q^3)/3 and
+// c1 = tr(Q^2)/2 through the eigenvalues 2u, -u + w, -u - w of Q.  For c0 < 0
+// the coefficients come from -Q: f_j(-c0) = (-1)^j conj(f_j(c0)).  With c0 >= 0
+// the denominator 9u^2 - w^2 is at least c1, so the form is well conditioned;
+// Q = 0 (c1 below 1e-12) goes to the Taylor series.  About a quarter of the FP64
+// work of expm3 (one matrix product and a few sines and cosines instead of ~18
+// products).
+__device__ __forceinline__ M3 expi_hermitian(const M3& Q) {
+  const M3 Q2 = mul(Q, Q);
+  const double c1 = 0.5 * (Q2.m[0].re + Q2.m[4].re + Q2.m[8].re);
+  if (!(c1 >= 1e-12)) {
+    M3 X;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) X.m[c] = {-Q.m[c].im, Q.m[c].re};
+    return expm3(X);
+  }
+  double t3 = 0.0;   // Re tr(Q Q^2)
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t3 += Q.m[3 * i + k].re * Q2.m[3 * k + i].re - Q.m[3 * i + k].im * Q2.m[3 * k + i].im;
+  const double c0s = t3 / 3.0;
+  const bool neg = c0s < 0.0;
+  const double c0 = fabs(c0s);
+  const double r = sqrt(c1 / 3.0);
+  const double c0max = 2.0 * r * r * r;
+  const double theta = acos(fmin(1.0, c0 / c0max));
+  double s3, c3;
+  sincos(theta / 3.0, &s3, &c3);
+  const double u = r * c3, w = sqrt(c1) * s3;
+  const double u2 = u * u, w2 = w * w;
+  double su, cu, sw, cw;
+  sincos(u, &su, &cu);
+  sincos(w, &sw, &cw);
+  // sin(w)/w, by its series near w = 0
+  const double xi0 = fabs(w) > 0.05 ? sw / w : 1.0 - w2 / 6.0 * (1.0 - w2 / 20.0 * (1.0 - w2 / 42.0));
+  const cplx<double> e2 = {cu * cu - su * su, 2.0 * su * cu};   // exp(2iu)
+  const cplx<double> em = {cu, -su};                            // exp(-iu)
+  const cplx<double> h0 = (u2 - w2) * e2 + cmul(em, cplx<double>{8.0 * u2 * cw, 2.0 * u * (3.0 * u2 + w2) * xi0});
+  const cplx<double> h1 = (2.0 * u) * e2 - cmul(em, cplx<double>{2.0 * u * cw, -(3.0 * u2 - w2) * xi0});
+  const cplx<double> h2 = e2 - cmul(em, cplx<double>{cw, 3.0 * u * xi0});
+  const double inv = 1.0 / (9.0 * u2 - w2);
+  cplx<double> f0 = inv * h0, f1 = inv * h1, f2 = inv * h2;
+  if (neg) {
+    f0 = conjg(f0);
+    f1 = -conjg(f1);
+    f2 = conjg(f2);
+  }
+  M3 E;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) E.m[c] = cmul(f1, Q.m[c]) + cmul(f2, Q2.m[c]);
+  E.m[0] = E.m[0] + f0;
+  E.m[4] = E.m[4] + f0;
+  E.m[8] = E.m[8] + f0;
   return E;
 }
 
