@@ -698,7 +698,7 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
     cudaMemcpyAsync(w->st, w->st_host, sizeof(BatchState), cudaMemcpyHostToDevice, st);
   }
   const BatchDesc bd = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, w->tile);
-  // FP64 passes (~140 registers per thread) use tiles of about 128 threads
+  // FP64 passes (~250 registers per thread) use tiles of about 128 threads
   const BatchDesc bd64 = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, std::max(nrhs, 128 / nrhs * nrhs));
   const int grid = std::min(bd.ntiles, w->grid_cap);
   batch_init(w, bd, inner_prec, grid, st);

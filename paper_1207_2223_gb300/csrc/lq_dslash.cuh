@@ -116,8 +116,9 @@ __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, cons
   }
 }
 
-// Threads per block: 256 for FP32 arithmetic; 128 for FP64, whose ~140
-// registers per thread would otherwise leave one block per SM.
+// Threads per block: 256 for FP32 arithmetic; 128 for FP64 and double-float,
+// whose 190-250 registers per thread would otherwise leave one block per SM
+// (the FP64 pipe, not occupancy, bounds the FP64 operator).
 template <typename T> struct DslashBlock { static constexpr int value = 256; };
 template <> struct DslashBlock<double> { static constexpr int value = 128; };
 template <> struct DslashBlock<df64> { static constexpr int value = 128; };
