@@ -6,14 +6,15 @@ U = exp(iA), A traceless Hermitian with N(0, 0.25^2) entries (seed 2),
 kappa = 0.156, antiperiodic time, a complex Gaussian source; M^dag M x = phi
 is solved from x0 = 0 to an FP64 true relative residual of 1e-10.
 
-One step = one mixed-precision solve (inner precision --inner, default
-16-bit fixed-point storage with 12-real links and per-site norms, FP32
-arithmetic, FP64 reliable updates every 50 iterations).  Printed as one JSON line:
+One step = one mixed-precision solve (inner precision --inner, default FP16
+storage with 12-real links and per-site FP32 norms, FP32 arithmetic, FP64
+reliable updates every 50 iterations).  Printed as one JSON line:
   value         solves per second over all ranks (device-timed, data resident)
   e2e           the same through the C interface with pinned host buffers
                 (gauge field and source copied in, solution copied out, every step)
-  roofline      the Dslash of the inner precision, timed with CUDA events on
-                the library's stream, against the measured HBM copy bandwidth
+  roofline      CG pass 2 of the inner precision (the largest kernel of the
+                solve), timed with CUDA events on the library's stream, against
+                the measured HBM copy bandwidth
   fp64          the plain FP64 CG on the same source (the comparison of the metric)
   cpu_baseline  the FP64 CPU oracle on a bounded sample, scaled to solves/s
 
@@ -49,23 +50,27 @@ DSLASH_BYTES = {k: GAUGE_B[k] + 2 * SPINOR_B[k] for k in GAUGE_B}
 #   k1  t = M p, |t|^2                          gauge + p + t
 #   k2  r -= alpha M^dag t, x += alpha p, |r|^2  gauge + t + r (read, write) + x (read, write) + p
 #   k3  p = r + beta p                          r + p (read, write)
-CG_BYTES = {k: {"k1": GAUGE_B[k] + 2 * SPINOR_B[k], "k2": GAUGE_B[k] + 6 * SPINOR_B[k], "k3": 3 * SPINOR_B[k]}
-            for k in GAUGE_B}
+# the low-precision solution x is stored in FP32 when the iteration vectors are 16-bit
+X_B = {k: (96 if SPINOR_B[k] == 52 else SPINOR_B[k]) for k in SPINOR_B}
+CG_BYTES = {k: {"k1": GAUGE_B[k] + 2 * SPINOR_B[k], "k2": GAUGE_B[k] + 4 * SPINOR_B[k] + 2 * X_B[k],
+                "k3": 3 * SPINOR_B[k]} for k in GAUGE_B}
 DSLASH_FLOPS = 1368
 # DRAM traffic per site of the plain Dslash from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum over sites), valid for the kernel sources with this
 # hash; see profiles/.  Null when the kernel changed since the capture.
 NCU_TRAFFIC = {
+    # profiles/cg_pass2_f16_12_32x32x32x32.md
+    "f16_12": {"bytes_per_site": 466.8, "src": "7096fb597015318a"},
     # profiles/cg_pass2_i16_12_32x32x32x32.md
-    "i16_12": {"bytes_per_site": 384.3, "src": "c1cf8879eeafeb7b"},
+    "i16_12": {"bytes_per_site": 464.9, "src": "7096fb597015318a"},
     # profiles/cg_pass2_f32_12_32x32x32x32.md
-    "f32_12": {"bytes_per_site": 755.4, "src": "c1cf8879eeafeb7b"},
+    "f32_12": {"bytes_per_site": 755.4, "src": "7096fb597015318a"},
 }
 
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("lq_device.cuh", "lq_dslash.cuh"):
+    for f in ("lq_device.cuh", "lq_dslash.cuh", "lq_internal.h", "k_cglo.cu"):
         h.update(open(os.path.join(ROOT, "paper_1207_2223_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -158,7 +163,7 @@ def measure_extras(lq, torch, dev):
         chi = torch.from_numpy(chi_noise(lat, 1)).to(dev)
         u = metropolis_uniform(1)
         hmc = {}
-        runs = (("f64", lq.LQ_F64), ("mixed_i16_12", lq.LQ_I16_12)) if dims[0] == 16 else (("mixed_i16_12", lq.LQ_I16_12),)
+        runs = (("f64", lq.LQ_F64), ("mixed_f16_12", lq.LQ_F16_12)) if dims[0] == 16 else (("mixed_f16_12", lq.LQ_F16_12),)
         for name, prec in runs:
             ctx = lq.lq_create(dims, True, torch.cuda.current_stream(dev).cuda_stream)
             try:
@@ -185,15 +190,15 @@ def measure_extras(lq, torch, dev):
     try:
         lq.lq_gauge_set(ctx, U)
         x = torch.zeros_like(phis)
-        lq.lq_solve_batch([ctx], [x], [phis], [0.155], 12, 1e-10, 20000, lq.LQ_I16_12, 50)   # autotune
+        lq.lq_solve_batch([ctx], [x], [phis], [0.155], 12, 1e-10, 20000, lq.LQ_F16_12, 50)   # autotune
         t0 = time.perf_counter()
         status, st, iters, resid, _ = lq.lq_solve_batch([ctx], [x], [phis], [0.155], 12, 1e-10, 20000,
-                                                        lq.LQ_I16_12, 50)
+                                                        lq.LQ_F16_12, 50)
         tb = time.perf_counter() - t0
         t0 = time.perf_counter()
         for i in range(12):
             xs = torch.zeros_like(phis[i])
-            lq.lq_solve_MdagM(ctx, xs, phis[i], 0.155, 1e-10, 20000, lq.LQ_I16_12, 50)
+            lq.lq_solve_MdagM(ctx, xs, phis[i], 0.155, 1e-10, 20000, lq.LQ_F16_12, 50)
         ts = time.perf_counter() - t0
     finally:
         lq.lq_destroy(ctx)
@@ -465,19 +470,21 @@ def run_ours(args):
         cg["iteration_ms"] = round(lq.lq_time_cg_kernel(ctx, phid, KAPPA, 0, inner, 40), 5)
         # the two-site packed FP32x2 variant of the 16-bit passes (LQ_OPT_PAIR_SITES, off by
         # default: fewer instructions, same FMA-pipe time, lower occupancy)
-        two_site = None
-        if args.inner == "i16_12":
-            lq.lq_set_option(ctx, lq.LQ_OPT_PAIR_SITES, 1)
-            two_site = {w: round(lq.lq_time_cg_kernel(ctx, phid, KAPPA, int(w[1]), inner, 40), 5)
-                        for w in ("k1", "k2")}
-            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            q0.record(stream)
-            sto = solve(inner)
-            q1.record(stream)
-            torch.cuda.synchronize(dev)
-            two_site["solve_s"] = q0.elapsed_time(q1) / 1e3
-            two_site["iterations"] = sto["iterations"]
-            lq.lq_set_option(ctx, lq.LQ_OPT_PAIR_SITES, 0)
+        # (16-bit fixed point only), against the one-site passes of the same format
+        i16 = lq.LQ_I16_12
+        two_site = {"one_site": {w: round(lq.lq_time_cg_kernel(ctx, phid, KAPPA, int(w[1]), i16, 40), 5)
+                                 for w in ("k1", "k2")}}
+        lq.lq_set_option(ctx, lq.LQ_OPT_PAIR_SITES, 1)
+        two_site.update({w: round(lq.lq_time_cg_kernel(ctx, phid, KAPPA, int(w[1]), i16, 40), 5)
+                         for w in ("k1", "k2")})
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        sto = solve(i16)
+        q1.record(stream)
+        torch.cuda.synchronize(dev)
+        two_site["solve_s"] = q0.elapsed_time(q1) / 1e3
+        two_site["iterations"] = sto["iterations"]
+        lq.lq_set_option(ctx, lq.LQ_OPT_PAIR_SITES, 0)
         src_hash = kernel_source_hash()
         tr = NCU_TRAFFIC.get(args.inner)
         traffic = tr["bytes_per_site"] * V if tr and tr.get("src") == src_hash else None
@@ -573,7 +580,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--inner", default="i16_12", choices=["f32", "f32_12", "f16_12", "bf16_12", "i16_12"])
+    ap.add_argument("--inner", default="f16_12", choices=["f32", "f32_12", "f16_12", "bf16_12", "i16_12"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extras", action="store_true", help="skip the HMC, batch and iteration-scan numbers")
     ap.add_argument("--ref-site-fraction", type=int, default=8)

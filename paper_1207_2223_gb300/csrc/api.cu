@@ -123,7 +123,7 @@ lq_status ensure_solver_fields(lq_ctx* c, int inner) {
     LQ_TRY(alloc_field(c, c->r_lo[k], s));
     LQ_TRY(alloc_field(c, c->p_lo[k], s));
     LQ_TRY(alloc_field(c, c->t_lo[k], s));
-    LQ_TRY(alloc_field(c, c->x_lo[k], s));
+    LQ_TRY(alloc_field(c, c->x_lo[k], xlo_store(s)));
   }
   return LQ_OK;
 }

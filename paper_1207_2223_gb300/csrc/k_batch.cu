@@ -165,7 +165,7 @@ struct BEpiCG2 {                             // r -= alpha M^dag t, x += alpha p
     const T alpha = (T)st->alpha[col];
     cplx<T> rv[12], xv[12], pv[12];
     load_spinor<S, T, false>(r, total, e, rv);
-    load_spinor<S, T, false>(x, total, e, xv);
+    load_spinor<xlo_store(S), T, false>(x, total, e, xv);
     load_spinor<S, T>(p, total, e, pv);
     T a = (T)0;
 #pragma unroll
@@ -178,7 +178,7 @@ struct BEpiCG2 {                             // r -= alpha M^dag t, x += alpha p
       a = fma(rv[k].im, rv[k].im, a);
     }
     store_spinor<S, T>(r, total, e, rv);
-    store_spinor<S, T>(x, total, e, xv);
+    store_spinor<xlo_store(S), T>(x, total, e, xv);
     return (double)a;
   }
   __device__ void finalize_cols(const double* tot, int ncols) const {
@@ -358,7 +358,7 @@ __global__ void batch_init_kernel(BatchDesc bd, SpinorRef phi64, SpinorRef x64, 
       }
       store_spinor<SStore::F64, double>(phi64, bd.total, e, a);
       store_spinor<SStore::F64, double>(x64, bd.total, e, z);
-      store_spinor<S, double>(xlo, bd.total, e, z);
+      store_spinor<xlo_store(S), double>(xlo, bd.total, e, z);
       store_spinor<S, double>(rlo, bd.total, e, a);
       store_spinor<S, double>(plo, bd.total, e, a);
     }
@@ -382,12 +382,12 @@ template <SStore S>
 __global__ void batch_accumulate_kernel(int total, SpinorRef xlo, SpinorRef x64) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     cplx<double> a[12], b[12], z[12];
-    load_spinor<S, double, false>(xlo, total, e, a);
+    load_spinor<xlo_store(S), double, false>(xlo, total, e, a);
     load_spinor<SStore::F64, double, false>(x64, total, e, b);
 #pragma unroll
     for (int q = 0; q < 12; ++q) { b[q] = b[q] + a[q]; z[q] = {0.0, 0.0}; }
     store_spinor<SStore::F64, double>(x64, total, e, b);
-    store_spinor<S, double>(xlo, total, e, z);
+    store_spinor<xlo_store(S), double>(xlo, total, e, z);
   }
 }
 
@@ -629,7 +629,7 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
     };
     const SStore slo = spinor_store_of(inner_prec);
     alloc(w->phi64, SStore::F64); alloc(w->x64, SStore::F64); alloc(w->r64, SStore::F64); alloc(w->tmp64, SStore::F64);
-    alloc(w->plo, slo); alloc(w->tlo, slo); alloc(w->rlo, slo); alloc(w->xlo, slo);
+    alloc(w->plo, slo); alloc(w->tlo, slo); alloc(w->rlo, slo); alloc(w->xlo, xlo_store(slo));
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     w->grid_cap = std::max(1, sms) * 4;

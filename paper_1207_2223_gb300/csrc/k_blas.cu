@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(kBS) solver_init_kernel(int V, SpinorRef phi64
     load_spinor<SStore::F64, double>(phi64, V, s, v);
 #pragma unroll
     for (int k = 0; k < 12; ++k) { red[0] += v[k].re * v[k].re + v[k].im * v[k].im; z[k] = {0.0, 0.0}; }
-    store_spinor<S, double>(x, V, s, z);
+    store_spinor<xlo_store(S), double>(x, V, s, z);
     store_spinor<S, double>(r, V, s, v);
     store_spinor<S, double>(p, V, s, v);
   }
@@ -61,12 +61,12 @@ __global__ void __launch_bounds__(kBS) accumulate_x_kernel(int V, SpinorRef xlo,
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
   cplx<double> a[12], b[12], z[12];
-  load_spinor<S, double, false>(xlo, V, s, a);
+  load_spinor<xlo_store(S), double, false>(xlo, V, s, a);
   load_spinor<SStore::F64, double, false>(xhi, V, s, b);
 #pragma unroll
   for (int k = 0; k < 12; ++k) { b[k] = b[k] + a[k]; z[k] = {0.0, 0.0}; }
   store_spinor<SStore::F64, double>(xhi, V, s, b);
-  store_spinor<S, double>(xlo, V, s, z);
+  store_spinor<xlo_store(S), double>(xlo, V, s, z);
 }
 
 template <SStore S>
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kBS) inner_restart_kernel(int V, SpinorRef src
   load_spinor<SStore::F64, double>(src64, V, s, v);
 #pragma unroll
   for (int k = 0; k < 12; ++k) z[k] = {0.0, 0.0};
-  store_spinor<S, double>(x, V, s, z);
+  store_spinor<xlo_store(S), double>(x, V, s, z);
   store_spinor<S, double>(r, V, s, v);
   store_spinor<S, double>(p, V, s, v);
 }
@@ -116,7 +116,7 @@ __global__ void state_after_residual_kernel(SolverState* st, int restart) {
 
 void launch_solver_init(const Geom& g, SpinorRef phi64, SStore sx, SpinorRef x, SStore sr, SpinorRef r,
                         SStore sp, SpinorRef p, SolverState* st, const ReduceScratch& rs, cudaStream_t stream) {
-  (void)sr; (void)sp;   // x, r and p always share one format
+  (void)sr; (void)sp;   // r and p share one format; x is stored as xlo_store() of it
   const int grid = grid_for(g.V, kBS);
   LQ_DISPATCH_S(sx, (solver_init_kernel<SS><<<grid, kBS, 0, stream>>>(g.V, phi64, x, r, p, st, rs)));
 }

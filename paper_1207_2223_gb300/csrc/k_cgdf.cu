@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kBS) accumulate_df_kernel(int V, SpinorRef xlo
   if (s >= V) return;
   cplx<float> a[12], z[12];
   cplx<df64> b[12];
-  load_spinor<SLO, float, false>(xlo, V, s, a);
+  load_spinor<xlo_store(SLO), float, false>(xlo, V, s, a);
   load_spinor<SStore::DF64, df64, false>(xdf, V, s, b);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kBS) accumulate_df_kernel(int V, SpinorRef xlo
     z[k] = {0.f, 0.f};
   }
   store_spinor<SStore::DF64, df64>(xdf, V, s, b);
-  store_spinor<SLO, float>(xlo, V, s, z);
+  store_spinor<xlo_store(SLO), float>(xlo, V, s, z);
 }
 
 // x = 0, r = p = src (double-float) in format S
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kBS) inner_restart_df_kernel(int V, SpinorRef 
   load_spinor<SStore::DF64, df64>(src, V, s, v);
 #pragma unroll
   for (int k = 0; k < 12; ++k) z[k] = {df64(0.f), df64(0.f)};
-  store_spinor<S, df64>(x, V, s, z);
+  store_spinor<xlo_store(S), df64>(x, V, s, z);
   store_spinor<S, df64>(r, V, s, v);
   store_spinor<S, df64>(p, V, s, v);
 }

@@ -13,7 +13,7 @@ static void iteration(lq_ctx* c, const void* gauge, double kappa, cudaStream_t s
   const int k = (int)S;
   EpiCG1<S> e1{c->t_lo[k].ref(), c->state};
   launch_dslash<float, G, S, false>(g, U, c->p_lo[k].ref(), kappa, e1, c->rs, stream);
-  EpiCG2<S, S, S> e2{c->r_lo[k].ref(), c->x_lo[k].ref(), c->p_lo[k].ref(), c->state};
+  EpiCG2<S, xlo_store(S), S> e2{c->r_lo[k].ref(), c->x_lo[k].ref(), c->p_lo[k].ref(), c->state};
   launch_dslash<float, G, S, true>(g, U, c->t_lo[k].ref(), kappa, e2, c->rs, stream);
   launch_xpay_p(g, S, c->r_lo[k].ref(), c->p_lo[k].ref(), c->state, false, stream);
 }
@@ -27,7 +27,7 @@ static void step(lq_ctx* c, const void* gauge, int which, double kappa, cudaStre
     EpiCG1<S> e1{c->t_lo[k].ref(), c->state};
     launch_dslash<float, G, S, false>(g, U, c->p_lo[k].ref(), kappa, e1, c->rs, stream);
   } else {
-    EpiCG2<S, S, S> e2{c->r_lo[k].ref(), c->x_lo[k].ref(), c->p_lo[k].ref(), c->state};
+    EpiCG2<S, xlo_store(S), S> e2{c->r_lo[k].ref(), c->x_lo[k].ref(), c->p_lo[k].ref(), c->state};
     launch_dslash<float, G, S, true>(g, U, c->t_lo[k].ref(), kappa, e2, c->rs, stream);
   }
 }

@@ -38,6 +38,15 @@ inline SStore spinor_store_of(int prec) {
   }
 }
 size_t spinor_bytes(SStore s, int V);        // chunk array only
+
+// Storage of the low-precision solution x of a mixed solve: FP32 when the
+// iteration vectors are 16-bit.  x is read and written once per iteration
+// (not by the stencil), so FP32 costs 44 B per site each way.  It saves the
+// per-site encode and decode of x in CG pass 2, and it keeps the accumulated
+// correction free of 16-bit rounding.
+constexpr SStore xlo_store(SStore s) {
+  return (s == SStore::F16 || s == SStore::BF16 || s == SStore::I16) ? SStore::F32 : s;
+}
 size_t gauge_bytes(GStore g, int V);
 
 // A spinor field in one storage format, owned by the context.

@@ -99,6 +99,25 @@ __device__ __forceinline__ void store_q(const SpinorRef& f, int V, int n0, int n
   }
 }
 
+// FP32 spinor (float4 [6][V]) at sites n0, n1 as complex pairs, and back
+__device__ __forceinline__ void load_f32(const SpinorRef& f, int V, int n0, int n1, c2 v[12]) {
+  const float4* p = static_cast<const float4*>(f.p);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float4 a = p[(size_t)k * V + n0], b = p[(size_t)k * V + n1];
+    v[2 * k] = {f2(a.x, b.x), f2(a.y, b.y)};
+    v[2 * k + 1] = {f2(a.z, b.z), f2(a.w, b.w)};
+  }
+}
+__device__ __forceinline__ void store_f32(const SpinorRef& f, int V, int n0, int n1, const c2 v[12]) {
+  float4* p = static_cast<float4*>(f.p);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    p[(size_t)k * V + n0] = make_float4(v[2 * k].re.x, v[2 * k].im.x, v[2 * k + 1].re.x, v[2 * k + 1].im.x);
+    p[(size_t)k * V + n1] = make_float4(v[2 * k].re.y, v[2 * k].im.y, v[2 * k + 1].re.y, v[2 * k + 1].im.y);
+  }
+}
+
 // conj(a b - c d)
 __device__ __forceinline__ c2 cross_conj(c2 a, c2 b, c2 c, c2 d) {
   const float2 x = fma2(c.im, d.im, mul(a.re, b.re));
@@ -342,8 +361,8 @@ struct PairCG1 : EpiCG1<SStore::I16> {                 // t = M p, |t|^2
   }
 };
 
-// r -= alpha M^dag t, x += alpha p, |r|^2
-struct PairCG2 : EpiCG2<SStore::I16, SStore::I16, SStore::I16> {
+// r -= alpha M^dag t, x += alpha p, |r|^2 (x in FP32, r and p 16-bit)
+struct PairCG2 : EpiCG2<SStore::I16, SStore::F32, SStore::I16> {
   __device__ void apply_pair(int V, int n0, int n1, pair::c2 v[12], double (&red)[NRED]) const {
     using namespace pair;
     const float a = (float)st->alpha;
@@ -360,17 +379,17 @@ struct PairCG2 : EpiCG2<SStore::I16, SStore::I16, SStore::I16> {
       store_q(r, V, n0, n1, rq);
       red[0] += norm2(rq);
     }
-    c2 xq[12], pq[12];
-    float2 nx, np;
-    load_q<false>(x, V, n0, n1, xq, nx);
+    c2 xv[12], pq[12];
+    float2 np;
+    load_f32(x, V, n0, n1, xv);
     load_q<true>(p, V, n0, n1, pq, np);
-    const float2 sx = mul(nx, f2(kQ16Inv, kQ16Inv)), sp = mul(np, f2(a * kQ16Inv, a * kQ16Inv));
+    const float2 sp = mul(np, f2(a * kQ16Inv, a * kQ16Inv));
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      xq[k].re = fma2(xq[k].re, sx, mul(pq[k].re, sp));
-      xq[k].im = fma2(xq[k].im, sx, mul(pq[k].im, sp));
+      xv[k].re = fma2(pq[k].re, sp, xv[k].re);
+      xv[k].im = fma2(pq[k].im, sp, xv[k].im);
     }
-    store_q(x, V, n0, n1, xq);
+    store_f32(x, V, n0, n1, xv);
   }
 };
 
