@@ -156,7 +156,9 @@ lq_status lq_apply_MdagM(lq_ctx* ctx, double* out, const double* in, double kapp
  * "conjugate gradient routine") from x0 = 0, until the FP64 true residual
  * ||phi - M^dag M x|| / ||phi|| <= tol.
  *   inner_prec      LQ_F64: plain FP64 CG.  Otherwise the iterations run
- *                   in that precision and the solution and residual are
+ *                   in that precision (the low-precision solution is kept
+ *                   in FP32 when the precision is a 16-bit format) and the
+ *                   solution and residual are
  *                   corrected in FP64 ("reliable updates"): at least every
  *                   `reliable_every` iterations (0 = only when the iterated
  *                   residual has dropped by 1e-2 since the last update, or
