@@ -102,8 +102,14 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.p.terminate()
         self.p.wait()
-        rows = [ln.split(",") for ln in open(self.f.name).read().splitlines() if ln.strip()]
+        text = open(self.f.name).read()
         os.unlink(self.f.name)
+        return self.summarise(text)
+
+    @staticmethod
+    def summarise(text):
+        """Median SM clock, maximum clock and the throttle reasons seen in nvidia-smi's CSV."""
+        rows = [ln.split(",") for ln in text.splitlines() if ln.strip()]
         sm = [float(r[1]) for r in rows if len(r) > 8 and r[1].strip().replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if len(r) > 8 and r[2].strip().replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
