@@ -8,7 +8,7 @@
 // and x' = (x, y, z, t + L_t/2), and every real of the arithmetic is the pair
 // (value at x, value at x') in one register pair, so one packed FP32x2
 // instruction (FFMA2 / FADD2 / FMUL2) does the work of two scalar ones.
-// Measured on GB300 it issues 35% fewer instructions but runs 7-12% slower:
+// Measured on GB300 it issues about a third fewer instructions but runs 8-15% slower:
 // a packed instruction holds the FMA pipe for two cycles, so the pipe time
 // per site does not change, and the doubled per-thread state lowers the
 // resident warps from 16 to 12 per SM.  It is therefore off by default.
