@@ -205,3 +205,29 @@ def test_full_size_trajectory_delta_H_scales_as_eps_squared(lq):
             lq.lq_destroy(ctx)
         dh.append(r["dH"])
     assert 3.8 < dh[0] / dh[1] < 4.2, dh
+
+
+def test_ensemble_exp_minus_dH_is_one(lq):
+    """A chain of 120 trajectories at 4^4 (beta 5.6, kappa 0.15, 10 steps, tau 1, FP64 solves,
+    momenta / noise / Metropolis numbers from their Philox streams): after 20 thermalisation
+    trajectories the equality <exp(-Delta H)> = 1 of an area-preserving, reversible
+    integrator holds within 3 standard errors, and the chain moves (about 30% of the
+    proposals are accepted at this step size, eps = 0.1).  The reductions are deterministic,
+    so the chain is the same on every run."""
+    dims = (4, 4, 4, 4)
+    lat = Lattice(dims)
+    ctx = _ctx(lq, dims, gauge_exp_iA(lat, 0.3, 11))
+    dh, acc = [], []
+    try:
+        for traj in range(120):
+            r = lq.lq_hmc_trajectory(ctx, dev(momenta(lat, 11, traj)), dev(chi_noise(lat, 11, traj)),
+                                     metropolis_uniform(11, traj), 5.6, 0.15, 10, 1.0, 1e-10, 10000,
+                                     lq.LQ_F64, 50)
+            dh.append(r["dH"])
+            acc.append(r["accepted"])
+    finally:
+        lq.lq_destroy(ctx)
+    e = np.exp(-np.array(dh[20:]))
+    err = e.std() / np.sqrt(len(e))
+    assert abs(e.mean() - 1.0) < 3 * err + 0.02, (e.mean(), err)
+    assert np.mean(acc[20:]) > 0.2
