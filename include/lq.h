@@ -119,8 +119,8 @@ lq_status lq_set_stream(lq_ctx* ctx, void* cuda_stream);
  *   LQ_OPT_DF64_UPDATES 0 (default): every reliable update of a mixed-precision solve in
  *                       FP64; 1: the intermediate ones in double-float arithmetic (LQ_DF64)
  *                       on the FP32 pipe, the final residual certified in FP64.  (On this
- *                       part the double-float operator is only ~1.3x faster than FP64, so
- *                       the extra certification pass makes option 1 slower overall.)
+ *                       part the double-float operator is only ~1.3x faster than FP64, and
+ *                       the extra certification pass eats the gain: both take the same time.)
  *   LQ_OPT_PAIR_SITES   0 (default): one site per thread; 1: with LQ_I16_12 and an even
  *                       L_t, the operator and the CG passes apply the stencil at two sites
  *                       per thread (x and x + L_t/2 in time) with packed FP32x2 arithmetic.
