@@ -60,18 +60,24 @@ DSLASH_FLOPS = 1368
 # hash; see profiles/.  Null when the kernel changed since the capture.
 NCU_TRAFFIC = {
     # profiles/cg_pass2_f16_12_32x32x32x32.md
-    "f16_12": {"bytes_per_site": 466.8, "src": "7096fb597015318a"},
+    "f16_12": {"bytes_per_site": 466.8, "src": "87e450e4b735615e"},
     # profiles/cg_pass2_i16_12_32x32x32x32.md
-    "i16_12": {"bytes_per_site": 464.9, "src": "7096fb597015318a"},
+    "i16_12": {"bytes_per_site": 464.9, "src": "87e450e4b735615e"},
     # profiles/cg_pass2_f32_12_32x32x32x32.md
-    "f32_12": {"bytes_per_site": 755.4, "src": "7096fb597015318a"},
+    "f32_12": {"bytes_per_site": 755.4, "src": "87e450e4b735615e"},
 }
 
 
 def kernel_source_hash():
+    """Hash of the code (comments and blank space removed) of the files that define the
+    CG passes, so that a comment edit does not void the traffic figures."""
+    import re
     h = hashlib.sha256()
     for f in ("lq_device.cuh", "lq_dslash.cuh", "lq_internal.h", "k_cglo.cu"):
-        h.update(open(os.path.join(ROOT, "paper_1207_2223_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_1207_2223_gb300", "csrc", f)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

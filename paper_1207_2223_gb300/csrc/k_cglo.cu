@@ -1,6 +1,7 @@
 // Low-precision CG iteration for mixed-precision solves: the same three
 // fused passes as the FP64 iteration, on FP32 or 16-bit storage with FP32
-// arithmetic and FP64 reductions.  The FP64 solution and residual are
+// arithmetic and FP64 reductions; the low-precision solution x is FP32 for
+// the 16-bit formats (xlo_store).  The FP64 solution and residual are
 // corrected by reliable updates driven from the host (api.cu).
 #include "lq_internal.h"
 
