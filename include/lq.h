@@ -158,15 +158,16 @@ lq_status lq_apply_MdagM(lq_ctx* ctx, double* out, const double* in, double kapp
  *   inner_prec      LQ_F64: plain FP64 CG.  Otherwise the iterations run
  *                   in that precision (the low-precision solution is kept
  *                   in FP32 when the precision is a 16-bit format) and the
- *                   solution and residual are
- *                   corrected in FP64 ("reliable updates"): at least every
- *                   `reliable_every` iterations (0 = only when the iterated
- *                   residual has dropped by 1e-2 since the last update, or
- *                   has met tol) the low-precision solution is added to
- *                   the FP64 one and the FP64 residual is recomputed.  If
- *                   three reliable updates in a row fail to halve the true
- *                   residual, the iterations continue in FP32 from there
- *                   (counted in stats->escalations).
+ *                   solution and residual are corrected in FP64 ("reliable
+ *                   updates"): the low-precision solution is added to the
+ *                   FP64 one and the FP64 residual is recomputed after
+ *                   `reliable_every` iterations (0: no fixed interval), or
+ *                   sooner when the iterated residual has dropped by a
+ *                   factor 100 since the last update (10 for LQ_BF16_12),
+ *                   and when it has met tol.  If three reliable updates in
+ *                   a row fail to halve the true residual, the iterations
+ *                   continue in FP32 from there (counted in
+ *                   stats->escalations).
  *   maxiter         iteration limit (> 0)
  *   hist, hist_len  optional host array receiving the relative iterated
  *                   residual of each iteration (NULL / 0 to skip)
