@@ -55,15 +55,13 @@ X_B = {k: (96 if SPINOR_B[k] == 52 else SPINOR_B[k]) for k in SPINOR_B}
 CG_BYTES = {k: {"k1": GAUGE_B[k] + 2 * SPINOR_B[k], "k2": GAUGE_B[k] + 4 * SPINOR_B[k] + 2 * X_B[k],
                 "k3": 3 * SPINOR_B[k]} for k in GAUGE_B}
 DSLASH_FLOPS = 1368
-# DRAM traffic per site of the plain Dslash from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum over sites), valid for the kernel sources with this
-# hash; see profiles/.  Null when the kernel changed since the capture.
+# DRAM traffic per site of CG pass 2 (r -= alpha M^dag t, x += alpha p, |r|^2) from one
+# ncu capture per storage format: dram__bytes_read.sum + dram__bytes_write.sum of a
+# single launch on a 32^4 lattice, divided by its 1,048,576 sites.  Valid for the kernel
+# sources with this hash; null once the kernel has changed since the capture.
 NCU_TRAFFIC = {
-    # profiles/cg_pass2_f16_12_32x32x32x32.md
     "f16_12": {"bytes_per_site": 466.8, "src": "87e450e4b735615e"},
-    # profiles/cg_pass2_i16_12_32x32x32x32.md
     "i16_12": {"bytes_per_site": 464.9, "src": "87e450e4b735615e"},
-    # profiles/cg_pass2_f32_12_32x32x32x32.md
     "f32_12": {"bytes_per_site": 755.4, "src": "87e450e4b735615e"},
 }
 
@@ -131,68 +129,253 @@ def make_inputs():
     return lat, gauge_exp_iA(lat, SIGMA, SEED), source(lat, SEED)
 
 
-def oracle_cg_iteration_seconds(U, phi, site_fraction=1):
-    """Time the oracle's work for one CG iteration (M^dag M plus the vector updates).
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
 
-    With site_fraction f > 1, M and M^dag are evaluated on a 1/f sample of the
-    sites (same operator code, gathered) and the time is scaled by f."""
+
+# ---- the FP64 oracle's CG, timed on the host cores (cpu_baseline and the reference arm)
+# Worker processes (started with spawn, never forked from a process that touched the GPU)
+# attach to the gauge field and the CG vectors in shared memory and each evaluates the
+# oracle's M or M^dag (oracle.wilson.apply_M, unchanged) on one slab of output sites.
+_W = {}
+
+
+def _oracle_worker_init(names, V, dims, kappa):
     import numpy as np
+    from multiprocessing import shared_memory
     from oracle.conventions import neighbours
+    _W["shm"] = {k: shared_memory.SharedMemory(name=n) for k, n in names.items()}
+    shape = {"U": (V, 4, 3, 3)}
+    _W["a"] = {k: np.ndarray(shape.get(k, (V, 4, 3)), dtype=np.complex128, buffer=m.buf)
+               for k, m in _W["shm"].items()}
+    _W["nbr"] = neighbours(dims, True)
+    _W["dims"], _W["kappa"] = dims, kappa
+
+
+def _oracle_worker_apply(job):
+    import numpy as np
     from oracle.wilson import apply_M
-    nbr = neighbours(DIMS, True)
+    src, dst, lo, hi, dagger = job
+    a = _W["a"]
+    a[dst][lo:hi] = apply_M(a["U"], a[src], _W["dims"], _W["kappa"], True, dagger, np.arange(lo, hi), _W["nbr"])
+    return hi - lo
+
+
+class OracleCG:
+    """Textbook CG on M^dag M with the FP64 oracle's operator, from x0 = 0, one iteration per
+    step().  With nproc > 1 each application of M / M^dag runs on nproc slabs of sites in a
+    process pool; the vector updates run in this process."""
+
+    def __init__(self, U, phi, nproc):
+        import numpy as np
+        self.np = np
+        self.V = U.shape[0]
+        self.nproc = nproc
+        self.pool = None
+        self.shm = []
+        if nproc > 1:
+            import multiprocessing as mp
+            from multiprocessing import shared_memory
+            names, arr = {}, {}
+            for k, like in (("U", U), ("p", phi), ("t", phi), ("s", phi)):
+                m = shared_memory.SharedMemory(create=True, size=like.nbytes)
+                self.shm.append(m)
+                names[k] = m.name
+                arr[k] = np.ndarray(like.shape, dtype=np.complex128, buffer=m.buf)
+            arr["U"][...] = U
+            self.a = arr
+            self.pool = mp.get_context("spawn").Pool(nproc, initializer=_oracle_worker_init,
+                                                     initargs=(names, self.V, DIMS, KAPPA))
+            self.pool.map(_oracle_worker_apply, [("p", "t", 0, 1, False)] * nproc)   # start every worker
+            edges = np.linspace(0, self.V, nproc + 1).astype(int)
+            self.slabs = [(int(a), int(b)) for a, b in zip(edges[:-1], edges[1:])]
+        else:
+            from oracle.conventions import neighbours
+            self.nbr = neighbours(DIMS, True)
+            self.a = {"U": U, "p": phi.copy(), "t": np.empty_like(phi), "s": np.empty_like(phi)}
+        self.x = np.zeros_like(phi)
+        self.r = phi.copy()
+        self.a["p"][...] = phi
+        self.rr = float(np.vdot(self.r, self.r).real)
+        self.phi2 = self.rr
+
+    def _apply(self, src, dst, dagger):
+        if self.pool is not None:
+            self.pool.map(_oracle_worker_apply, [(src, dst, lo, hi, dagger) for lo, hi in self.slabs])
+        else:
+            from oracle.wilson import apply_M
+            self.a[dst][...] = apply_M(self.a["U"], self.a[src], DIMS, KAPPA, True, dagger, None, self.nbr)
+
+    def step(self):
+        """One CG iteration; returns its wall-clock seconds."""
+        np = self.np
+        t0 = time.perf_counter()
+        self._apply("p", "t", False)               # t = M p
+        self._apply("t", "s", True)                # s = M^dag t = M^dag M p
+        p, t, s = self.a["p"], self.a["t"], self.a["s"]
+        alpha = self.rr / float(np.vdot(t, t).real)
+        self.x += alpha * p
+        self.r -= alpha * s
+        rr_new = float(np.vdot(self.r, self.r).real)
+        p *= rr_new / self.rr
+        p += self.r
+        self.rr = rr_new
+        return time.perf_counter() - t0
+
+    def rel_residual(self):
+        return (self.rr / self.phi2) ** 0.5
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+        self.a = None
+        for m in self.shm:
+            m.close()
+            m.unlink()
+        self.shm = []
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sampled_residual(U, phi, x, n_sites=200, seed=0):
+    """FP64 true relative residual of a solution x at sampled sites, evaluated by the oracle
+    (M^dag M x at each sampled site from its one-hop neighbourhood), relative to phi there."""
+    import numpy as np
+    from oracle.wilson import apply_MdagM_sites
     V = U.shape[0]
-    sites = None if site_fraction == 1 else np.arange(0, V, site_fraction)
-    t0 = time.perf_counter()
-    a = apply_M(U, phi, DIMS, KAPPA, True, False, sites, nbr)
-    b = apply_M(U, phi, DIMS, KAPPA, True, True, sites, nbr)
-    t1 = time.perf_counter()
-    x = phi.copy()
-    r = phi.copy()
-    alpha = 0.5
-    x = x + alpha * phi
-    r = r - alpha * phi
-    rr = np.vdot(r, r).real
-    p = r + (rr / (rr + 1.0)) * phi
-    t2 = time.perf_counter()
-    del a, b, x, r, p
-    return (t1 - t0) * site_fraction + (t2 - t1)
+    rng = np.random.default_rng(seed)
+    sites = np.unique(np.concatenate([rng.integers(0, V, n_sites), [0, V - 1]]))
+    Ax = apply_MdagM_sites(U, x, DIMS, KAPPA, sites)
+    r = phi[sites] - Ax
+    return float(np.linalg.norm(r) / np.linalg.norm(phi[sites])), int(len(sites))
+
+
+def hmc_chain(lq, torch, dev, dims, U, seed, n_traj, beta, kappa, steps, prec):
+    """n_traj HMC trajectories in one context from links U (device), with the heat bath
+    (momenta, noise, Metropolis uniform) drawn on the device from the generator's streams
+    (trajectories 0 .. n_traj - 1 of `seed`).  Returns a summary."""
+    import numpy as np
+    rows = []
+    ctx = lq.lq_create(dims, True, torch.cuda.current_stream(dev).cuda_stream)
+    try:
+        lq.lq_gauge_set(ctx, U)
+        for traj in range(n_traj):
+            rows.append(lq.lq_hmc_trajectory_seeded(ctx, seed, traj, beta, kappa, steps, 1.0, 1e-10, 20000, prec, 50))
+    finally:
+        lq.lq_destroy(ctx)
+    dev_t = [r["seconds_solve"] + r["seconds_gauge_force"] + r["seconds_fermion_force"] + r["seconds_link_update"]
+             for r in rows]
+    dh = np.array([r["dH"] for r in rows])
+    sec = np.array([r["seconds"] for r in rows])
+    return {"trajectories": n_traj, "seconds_per_trajectory": float(sec.mean()),
+            "trajectories_per_s": float(n_traj / sec.sum()), "dH": [float(v) for v in dh],
+            "acceptance": float(np.mean([r["accepted"] for r in rows])),
+            # undefined (overflows) while a chain still falls from a rough start with dH << 0
+            "exp_minus_dH_mean": float(np.mean(np.exp(-dh))) if np.all(dh > -700.0) else None,
+            "plaquette": [float(r["plaquette"]) for r in rows],
+            "cg_iterations_per_trajectory": float(np.mean([r["cg_iterations"] for r in rows])),
+            "solves_per_trajectory": rows[0]["solves"],
+            "share": {k: float(np.mean([r["seconds_" + k] / d for r, d in zip(rows, dev_t)]))
+                      for k in ("solve", "gauge_force", "fermion_force", "link_update")}}
 
 
 def measure_extras(lq, torch, dev):
-    """Numbers beside the headline, each measured once outside the timed region:
-    HMC trajectories at 16^4, the batched solve at 24^4 x 12, and CG time against
-    iteration count with and without CUDA graphs (per-call overhead = intercept)."""
+    """Numbers beside the headline, each measured once outside the timed region: the
+    other workloads (one trajectory at 4^4; 1000 operator applications, a solve and 5
+    trajectories at 16^4; trajectories at 32^4; the differentiable action at 16^4), the
+    per-routine split of trajectories across volumes, the batched solve at 24^4 x 12,
+    the register ablation, and CG time against iteration count with and without CUDA
+    graphs (per-call overhead = intercept)."""
     import numpy as np
-    from synth import Lattice, gauge_exp_iA, source, momenta, chi_noise, metropolis_uniform
+    from synth import Lattice, gauge_exp_iA, source
     out = {}
-    # HMC trajectories (beta 5.6, kappa 0.155, 20 leapfrog steps, tau 1, reunitarised exp(iA)
-    # start, sigma 0.3) with the per-routine device-time split, 8^4 to 24^4; FP64 and mixed
-    # solves at 16^4
-    for dims in ((8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 24)):
+    # one plain FP64 trajectory at 4^4 (beta 5.6, kappa 0.15, 10 steps, tau 1, sigma 0.3, seed 0)
+    lat = Lattice((4, 4, 4, 4))
+    U = torch.from_numpy(gauge_exp_iA(lat, 0.3, 0)).to(dev)
+    out["hmc_4x4x4x4_f64"] = hmc_chain(lq, torch, dev, (4, 4, 4, 4), U, 0, 1, 5.6, 0.15, 10, lq.LQ_F64)
+    # 16^4 (sigma 0.3, seed 1, reunitarised, kappa 0.155): 1000 applications of M in FP64 and
+    # FP32 (the lattice fits in L2), one solve to 1e-10, 5 trajectories (beta 5.6, 20 steps)
+    dims = (16, 16, 16, 16)
+    lat = Lattice(dims)
+    V16 = lat.V
+    U = torch.from_numpy(gauge_exp_iA(lat, 0.3, 1, reunitarise=True)).to(dev)
+    phi = torch.from_numpy(source(lat, 1)).to(dev)
+    c2 = {}
+    ctx = lq.lq_create(dims, True, torch.cuda.current_stream(dev).cuda_stream)
+    try:
+        lq.lq_gauge_set(ctx, U)
+        for name in ("f64", "f32"):
+            ms = lq.lq_time_dslash(ctx, phi, 0.155, False, lq.PRECISIONS[name], 1000, False)
+            c2["dslash_1000_" + name] = {"ms_per_application": ms,
+                                         "GB/s": DSLASH_BYTES[name] * V16 / (ms * 1e-3) / 1e9,
+                                         "GFLOP/s": DSLASH_FLOPS * V16 / (ms * 1e-3) / 1e9}
+        for name in ("f64", "f32", "f16_12"):
+            x = torch.zeros_like(phi)
+            t0 = time.perf_counter()
+            _, st = lq.lq_solve_MdagM(ctx, x, phi, 0.155, 1e-10, 20000, lq.PRECISIONS[name], 50)
+            c2["solve_" + name] = {"seconds": time.perf_counter() - t0, "iterations": st["iterations"],
+                                   "true_rel_resid": st["true_rel_resid"]}
+    finally:
+        lq.lq_destroy(ctx)
+    for name in ("f64", "f32", "f16_12"):
+        c2["hmc_5traj_" + name] = hmc_chain(lq, torch, dev, dims, U, 1, 5, 5.6, 0.155, 20, lq.PRECISIONS[name])
+    out["wilson_16x16x16x16"] = c2
+    # per-routine split of a trajectory (mixed FP16-12 solves) at 8^4 and 24^4, same parameters
+    for d in (8, 24):
+        dims = (d, d, d, d)
         lat = Lattice(dims)
         U = torch.from_numpy(gauge_exp_iA(lat, 0.3, 1, reunitarise=True)).to(dev)
-        p0 = torch.from_numpy(momenta(lat, 1)).to(dev)
-        chi = torch.from_numpy(chi_noise(lat, 1)).to(dev)
-        u = metropolis_uniform(1)
-        hmc = {}
-        runs = (("f64", lq.LQ_F64), ("mixed_f16_12", lq.LQ_F16_12)) if dims[0] == 16 else (("mixed_f16_12", lq.LQ_F16_12),)
-        for name, prec in runs:
-            ctx = lq.lq_create(dims, True, torch.cuda.current_stream(dev).cuda_stream)
-            try:
-                lq.lq_gauge_set(ctx, U)
-                r = lq.lq_hmc_trajectory(ctx, p0.clone(), chi, u, 5.6, 0.155, 20, 1.0, 1e-10, 20000, prec, 50)
-            finally:
-                lq.lq_destroy(ctx)
-            dev_total = r["seconds_solve"] + r["seconds_gauge_force"] + r["seconds_fermion_force"] + \
-                r["seconds_link_update"]
-            hmc[name] = {"seconds": r["seconds"], "trajectories_per_s": 1.0 / r["seconds"], "dH": r["dH"],
-                         "accepted": r["accepted"], "solves": r["solves"], "cg_iterations": r["cg_iterations"],
-                         "plaquette": r["plaquette"],
-                         "share": {"solve": r["seconds_solve"] / dev_total,
-                                   "gauge_force": r["seconds_gauge_force"] / dev_total,
-                                   "fermion_force": r["seconds_fermion_force"] / dev_total,
-                                   "link_update": r["seconds_link_update"] / dev_total}}
-        out["hmc_%dx%dx%dx%d" % dims] = hmc
+        out["hmc_%dx%dx%dx%d_f16_12" % dims] = hmc_chain(lq, torch, dev, dims, U, 1, 1, 5.6, 0.155, 20,
+                                                         lq.LQ_F16_12)
+    # 32^4 trajectories of the differentiable-action workload (beta 5.7, kappa 0.155, 25 steps,
+    # tau 1, mixed FP16-12 solves, exp(iA) start sigma 0.3 seed 8): the first 3 of its 20
+    dims = (32, 32, 32, 32)
+    lat = Lattice(dims)
+    U = torch.from_numpy(gauge_exp_iA(lat, 0.3, 8)).to(dev)
+    out["hmc_32x32x32x32_f16_12"] = hmc_chain(lq, torch, dev, dims, U, 8, 3, 5.7, 0.155, 25, lq.LQ_F16_12)
+    del U
+    # differentiable S_f at 16^4 (kappa 0.15, seed 8): forward + backward per step through the
+    # cached context (the first step creates it and records the solver's CUDA graphs)
+    from paper_1207_2223_gb300 import autograd as ag
+    dims = (16, 16, 16, 16)
+    lat = Lattice(dims)
+    Ua = torch.from_numpy(gauge_exp_iA(lat, 0.3, 8)).to(dev).requires_grad_(True)
+    phia = torch.from_numpy(source(lat, 8)).to(dev)
+    ag.release_contexts()
+    steps_s = []
+    for _ in range(6):
+        Ua.grad = None
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ag.pseudofermion_action(Ua, phia, dims, 0.15, 1e-10).backward()
+        torch.cuda.synchronize(dev)
+        steps_s.append(time.perf_counter() - t0)
+    out["autograd_16x16x16x16"] = {"first_step_s": steps_s[0], "step_s": float(np.median(steps_s[1:])),
+                                   "gauge_loads": list(ag.cached_context_stats().values())[0]}
+    ag.release_contexts()
+    del Ua, phia
     # batched solve: 24^4, kappa 0.155, seed 3, 12 right-hand sides sharing one gauge field
     dims = (24, 24, 24, 24)
     lat = Lattice(dims)
@@ -281,7 +464,7 @@ def run_hmc_ensemble(args):
     import numpy as np
     import torch
     import paper_1207_2223_gb300 as lq
-    from synth import Lattice, gauge_exp_iA, identity_gauge, momenta, chi_noise, metropolis_uniform
+    from synth import Lattice, gauge_exp_iA, identity_gauge
     dims = tuple(args.dims) if tuple(args.dims) != DIMS else (32, 32, 32, 32)
     lat = Lattice(dims)
     ctx = lq.lq_create(dims)
@@ -290,10 +473,8 @@ def run_hmc_ensemble(args):
     rows = []
     t0 = time.perf_counter()
     for traj in range(args.trajectories):
-        p = torch.from_numpy(momenta(lat, 8, traj)).cuda()
-        chi = torch.from_numpy(chi_noise(lat, 8, traj)).cuda()
-        r = lq.lq_hmc_trajectory(ctx, p, chi, metropolis_uniform(8, traj), args.beta, args.hmc_kappa,
-                                 args.md_steps, 1.0, 1e-10, 20000, lq.PRECISIONS[args.inner], 50)
+        r = lq.lq_hmc_trajectory_seeded(ctx, 8, traj, args.beta, args.hmc_kappa, args.md_steps, 1.0, 1e-10, 20000,
+                                        lq.PRECISIONS[args.inner], 50)
         rows.append(r)
         print(json.dumps({"traj": traj, "dH": r["dH"], "accepted": r["accepted"], "plaquette": r["plaquette"],
                           "seconds": r["seconds"], "cg_iterations": r["cg_iterations"]}), flush=True)
@@ -323,28 +504,69 @@ def run_hmc_ensemble(args):
     return 0
 
 
+def oracle_timing(U, phi, all_steps, warmup, single_steps):
+    """Time the FP64 oracle's CG on this host: `warmup` + `all_steps` iterations on every core
+    (process pool over site slabs), then `single_steps` iterations on one core.  Returns a
+    dict with the per-step times and the host description."""
+    import numpy as np
+    n = host_cores()
+    out = {"cores": n, "cpu_model": cpu_model(), "nproc": os.cpu_count()}
+    cg = OracleCG(U, phi, n)
+    try:
+        for _ in range(warmup):
+            cg.step()
+        t = [cg.step() for _ in range(all_steps)]
+        out["all_cores_s_per_iteration"] = t
+        out["all_cores_rel_residual_after"] = cg.rel_residual()
+    finally:
+        cg.close()
+    if single_steps > 0:
+        cg1 = OracleCG(U, phi, 1)
+        out["single_core_s_per_iteration"] = [cg1.step() for _ in range(single_steps)]
+        cg1.close()
+    out["iterations_done"] = warmup + all_steps
+    out["median_all"] = float(np.median(t)) if t else None
+    return out
+
+
+# FP64 CG iterations of the 32^3 x 64 workload to a 1e-10 true residual (measured with
+# the plain FP64 GPU CG, which follows the same algorithm from the same x0 = 0)
+FP64_ITERATIONS = 312
+
+
 def run_reference(args):
+    """The reference arm: the project's FP64 CPU oracle (written from the paper), as it stands,
+    on the host cores.  One step = one full CG iteration of the oracle on the whole 32^3 x 64
+    lattice (M and M^dag on all sites over a process pool, vector updates in the main
+    process); solves/s = 1 / (measured time per iteration x the FP64 iteration count)."""
     import numpy as np
     rank, size = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return 0
     lat, U, phi = make_inputs()
-    n_iter = args.cg_iterations
-    frac = args.ref_site_fraction
-    for _ in range(args.warmup):
-        oracle_cg_iteration_seconds(U, phi, frac)
-    t = [oracle_cg_iteration_seconds(U, phi, frac) for _ in range(args.steps)]
-    per_solve = float(np.mean(t)) * n_iter
-    value = 1.0 / per_solve
-    sample = ("one CG iteration of the FP64 oracle (M and M^dag on every %d-th site, scaled by %d, plus "
-              "the vector updates on the full lattice) per step, times %d iterations (the FP64 CG "
-              "iteration count of this workload)" % (frac, frac, n_iter))
+    tm = oracle_timing(U, phi, args.steps, args.warmup, 1 if args.single_core else 0)
+    t_it = tm["median_all"]
+    value = 1.0 / (t_it * FP64_ITERATIONS)
+    sample = ("one full FP64 CG iteration of the oracle per step (M and M^dag on all %d sites on %d host "
+              "processes, vector updates in one), solves/s = 1 / (median time per iteration x %d, the "
+              "iteration count of the FP64 CG on this workload)" % (lat.V, tm["cores"], FP64_ITERATIONS))
+    cpu = {"value": value, "unit": "solves/s", "cores": tm["cores"], "kind": "oracle", "sample": sample,
+           "cpu_model": tm["cpu_model"], "nproc": tm["nproc"],
+           "seconds_per_iteration_all_cores": t_it,
+           "iterations_per_solve": FP64_ITERATIONS}
+    if tm.get("single_core_s_per_iteration"):
+        t1 = float(np.median(tm["single_core_s_per_iteration"]))
+        cpu["single_core"] = {"seconds_per_iteration": t1, "value": 1.0 / (t1 * FP64_ITERATIONS),
+                              "unit": "solves/s"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": size,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3 / n_iter,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_it * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "dims": list(DIMS), "kappa": KAPPA,
                                             "sigma": SIGMA, "seed": SEED, "tol": TOL},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "step": "one FP64 CG iteration of the oracle; value = solves/s = 1 / (ms_per_step x %d)"
+                    % FP64_ITERATIONS,
+            "iterations_per_solve": FP64_ITERATIONS,
+            "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -428,6 +650,7 @@ def run_ours(args):
         t_job, units = replicas.combine(t_local, args.steps, dev)
         value = units / t_job
         launches = int(sum(s["kernel_launches"] for s in stats))
+        x_mixed = x.cpu().numpy()             # the timed solves' solution (checked by the oracle below)
 
         # the other inner storage formats, one solve each (FP16-12 is the storage the
         # 32^3 x 64 workload names; FP32-12 is HBM-bound, the 16-bit formats issue-bound)
@@ -463,6 +686,7 @@ def run_ours(args):
         t1.record(stream)
         torch.cuda.synchronize(dev)
         fp64_s = t0.elapsed_time(t1) / 1e3
+        x_fp64 = x.cpu().numpy()
 
         # kernels timed alone with CUDA events on the library's stream
         peaks, peak_kind = load_peaks()
@@ -473,6 +697,15 @@ def run_ours(args):
             gbs = DSLASH_BYTES[name] * V / (ms * 1e-3) / 1e9
             dsl[name] = {"ms": round(ms, 5), "GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4),
                          "GFLOP/s": round(DSLASH_FLOPS * V / (ms * 1e-3) / 1e9, 1)}
+        # the FP64 operator is bound by the FP64 pipe: its roofline is the measured FP64
+        # fused multiply-add rate of this GPU (FP32 rate for comparison)
+        fma = {"f64_tflops": lq.lq_time_fma_peak(ctx, lq.LQ_F64), "f32_tflops": lq.lq_time_fma_peak(ctx, lq.LQ_F32)}
+        d64 = dsl["f64"]
+        fp64_roofline = {"kernel": "dslash_kernel<f64> (M)", "bound": "alu",
+                         "achieved": round(d64["GFLOP/s"] / 1e3, 4), "peak": round(fma["f64_tflops"], 4),
+                         "unit": "TFLOP/s", "frac": round(d64["GFLOP/s"] / 1e3 / fma["f64_tflops"], 4),
+                         "peak_kind": "measured (lq_time_fma_peak: FP64 fused multiply-add chains)",
+                         "flop_per_site": DSLASH_FLOPS, "launch_ms": d64["ms"]}
         cg = {}
         for which in ("k1", "k2", "k3"):
             ms = lq.lq_time_cg_kernel(ctx, phid, KAPPA, int(which[1]), inner, 40)
@@ -549,13 +782,27 @@ def run_ours(args):
 
         cpu = None
         if rank == 0 and size == 1 and not args.no_cpu:
-            t_it = oracle_cg_iteration_seconds(U, phi, args.ref_site_fraction)
+            # the oracle on the host cores: a bounded sample of its FP64 CG on this workload
+            tm = oracle_timing(U, phi, 3, 1, 1)
+            t_all = tm["median_all"]
+            t_one = float(tm["single_core_s_per_iteration"][0])
             n_it = st64["iterations"]
-            cpu = {"value": 1.0 / (t_it * n_it), "unit": "solves/s", "cores": 1, "kind": "oracle",
-                   "sample": "one CG iteration of the FP64 oracle (M and M^dag on every %d-th site, scaled, "
-                             "plus the vector updates), times the %d iterations of the FP64 CG"
-                             % (args.ref_site_fraction, n_it),
-                   "seconds_per_iteration": t_it}
+            cpu = {"value": 1.0 / (t_all * n_it), "unit": "solves/s", "cores": tm["cores"], "kind": "oracle",
+                   "sample": "4 full FP64 CG iterations of the oracle (M and M^dag on all %d sites over %d host "
+                             "processes; the first untimed), median time per iteration x the %d iterations "
+                             "of the FP64 CG; then one iteration on a single core" % (V, tm["cores"], n_it),
+                   "cpu_model": tm["cpu_model"], "nproc": tm["nproc"],
+                   "seconds_per_iteration_all_cores": t_all,
+                   "single_core": {"seconds_per_iteration": t_one, "value": 1.0 / (t_one * n_it),
+                                   "unit": "solves/s"}}
+            # the oracle's own FP64 residual of the GPU solutions at sampled sites (config
+            # 3: FP64 oracle error reported for the solution)
+            check = {}
+            for name, xs in (("mixed", x_mixed), ("fp64", x_fp64)):
+                rel, ns = oracle_sampled_residual(U, phi, xs)
+                check[name] = rel
+            check["sites"] = ns
+            cpu["oracle_residual_of_gpu_solution"] = check
     finally:
         lq.lq_destroy(ctx)
 
@@ -575,7 +822,7 @@ def run_ours(args):
             "iterations": {"mixed": stats[-1]["iterations"], "reliable_updates": stats[-1]["reliable_updates"],
                            "fp64": st64["iterations"]},
             "true_rel_resid": {"mixed": stats[-1]["true_rel_resid"], "fp64": st64["true_rel_resid"]},
-            "roofline": roofline, "cg_kernels": cg, "cg_kernels_two_site": two_site, "dslash": dsl, "e2e": e2e,
+            "roofline": roofline, "fp64_roofline": fp64_roofline, "fma_peaks": fma, "cg_kernels": cg, "cg_kernels_two_site": two_site, "dslash": dsl, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk}
     if cpu is not None:
         line["cpu_baseline"] = cpu
@@ -595,9 +842,8 @@ def main():
     ap.add_argument("--inner", default="f16_12", choices=["f32", "f32_12", "f16_12", "bf16_12", "i16_12"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extras", action="store_true", help="skip the HMC, batch and iteration-scan numbers")
-    ap.add_argument("--ref-site-fraction", type=int, default=8)
-    ap.add_argument("--cg-iterations", type=int, default=312,
-                    help="FP64 CG iterations of this workload (reference arm extrapolation)")
+    ap.add_argument("--single-core", type=int, default=1, choices=[0, 1],
+                    help="--impl reference: also time one oracle CG iteration on a single core")
     ap.add_argument("--kernel-only", default=None, choices=["dslash", "k1", "k2", "k3", "batch"],
                     help="profiling target: only launch this kernel (precision --prec); batch: a 12-RHS "
                          "batched solve of --steps iterations")

@@ -126,8 +126,19 @@ lq_status lq_set_stream(lq_ctx* ctx, void* cuda_stream);
  *                       per thread (x and x + L_t/2 in time) with packed FP32x2 arithmetic.
  *                       Same operator, results differ only by FP32 rounding.  (On this part
  *                       option 1 issues 35% fewer instructions but is slower: a packed FMA
- *                       holds the FMA pipe for two cycles and the occupancy halves.) */
-enum { LQ_OPT_CUDA_GRAPHS = 1, LQ_OPT_DF64_UPDATES = 2, LQ_OPT_PAIR_SITES = 3 };
+ *                       holds the FMA pipe for two cycles and the occupancy halves.)
+ *   LQ_OPT_STAGED       0 (default): every thread loads and decodes the links of its eight hops;
+ *                       1: with an FP32-arithmetic precision, a block of 256 consecutive sites
+ *                       decodes each x and y link once for the forward hop of x and the backward
+ *                       hop of x+mu, handing the latter to the neighbour's thread through shared
+ *                       memory (Sec. 3 kernel 1 with in-block sharing); the operator and the CG
+ *                       passes.  Same operator, results differ only by FP32 rounding order.
+ *   LQ_OPT_BATCH_RHS_PER_THREAD  0 (default): lq_solve_batch tunes its launch shape; 1..4:
+ *                       every thread applies each link to this many right-hand sides (must
+ *                       divide nrhs), 256 threads per block, no timing.  Changing it drops
+ *                       the batch workspace of the context. */
+enum { LQ_OPT_CUDA_GRAPHS = 1, LQ_OPT_DF64_UPDATES = 2, LQ_OPT_PAIR_SITES = 3, LQ_OPT_STAGED = 4,
+       LQ_OPT_BATCH_RHS_PER_THREAD = 5 };
 lq_status lq_set_option(lq_ctx* ctx, int option, int value);
 
 /* Number of lattice sites V. */
@@ -185,15 +196,18 @@ lq_status lq_solve_MdagM(lq_ctx* ctx, double* x, const double* phi, double kappa
  * device) with nrhs right-hand sides phi[k] (device, canonical spinors stored
  * one after another: [nrhs][V_k][4][3] complex), solution x[k] (device, same
  * layout).  Right-hand sides of one system share its links, which are read
- * once per site for all of them.  Iterations run in FP32 arithmetic on the storage
- * of inner_prec (LQ_F32, LQ_F32_12, LQ_F16_12 or LQ_I16_12) with FP64 reliable updates
+ * once per site for all of them: a thread applies each decoded link to several right-hand
+ * sides held in registers.  Iterations run in FP32 arithmetic on the storage
+ * of inner_prec (LQ_F32, LQ_F32_12, LQ_F16_12, LQ_BF16_12 or LQ_I16_12) with FP64 reliable updates
  * every reliable_every iterations (sooner when a column's iterated residual fell by 1e-2,
  * 16-bit storage, or 1e-3, FP32; a column whose true residual turns out far above its
  * iterated one restarts its search direction);
  * a column (system x right-hand side) whose FP64 true residual meets tol is
- * frozen.  1 <= n <= 16, 1 <= nrhs <= 16, n * nrhs <= 64.  Block size is
- * picked by timing candidates on the first call (autotuning); the iterations
- * run as CUDA graphs on ctxs[0]'s stream, which owns the workspace.
+ * frozen.  1 <= n <= 16, 1 <= nrhs <= 16, n * nrhs <= 64.  The launch shape (threads
+ * per block, right-hand sides per thread, resident blocks per SM) is picked by timing
+ * the candidates on the first call for a batch shape (autotuning; lq_batch_tuning
+ * reports the choice); the iterations run as CUDA graphs on ctxs[0]'s stream, which
+ * owns the workspace.
  *   hist     optional host array [n * nrhs][hist_len]: relative iterated residual
  *            of every column per iteration
  *   iters    optional host int[n * nrhs]: iterations until each column was frozen
@@ -203,6 +217,15 @@ lq_status lq_solve_MdagM(lq_ctx* ctx, double* x, const double* phi, double kappa
 lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const double** phi, const double* kappa, int nrhs,
                          double tol, int maxiter, int inner_prec, int reliable_every, double* hist, int hist_len,
                          int* iters, double* resid, lq_solve_stats* stats);
+
+/* The launch shape the autotuner of lq_solve_batch picked for the last batch shape solved
+ * with ctx as ctxs[0]: threads per block (= sites per tile), right-hand sides per thread,
+ * resident blocks per SM (0: all that fit); ms[0 .. ms_len) receives the measured time of
+ * one iteration for every candidate in the order tried (rhs per thread 1, 2, 3, 4 among
+ * the divisors of nrhs; for each, 256 threads with all blocks, 256 threads with one block
+ * per SM, 128 threads).  Any output may be NULL.  Errors: LQ_ERR_STATE (no batched solve
+ * yet). */
+lq_status lq_batch_tuning(lq_ctx* ctx, int* tile, int* rhs_per_thread, int* blocks_per_sm, double* ms, int ms_len);
 
 /* ---------------------------------------------------------------- MD */
 
@@ -286,6 +309,36 @@ lq_status lq_link_update(lq_ctx* ctx, const double* p, double eps);
 lq_status lq_hmc_trajectory(lq_ctx* ctx, const lq_hmc_params* params, double* p, const double* chi, double u,
                             lq_traj_result* result);
 
+/* One HMC trajectory with its heat bath drawn on the device (Sec. 2: Gaussian momenta
+ * at the start of every trajectory; Sec. 3 step 1: chi Gaussian, phi = M^dag chi; Sec. 3
+ * step 3: the Metropolis test), otherwise as lq_hmc_trajectory.  The random numbers come
+ * from the counter-based generator Philox4x32-10 (Salmon et al., SC'11) with key
+ * (seed, stream) and counters (all 32-bit words):
+ *   momenta  stream 1, counter (site, mu + 4 traj_index, k, 0), k = 0..3: coefficients
+ *            2k, 2k+1 of link (site, mu) are the Box-Muller pair of call k
+ *   chi      stream 2, counter (site, traj_index, k, 0), k = 0..11: complex component
+ *            k = 3 spin + colour is (z0 + i z1) sqrt(1/2)
+ *   u        stream 3, counter (traj_index, 0, 0, 0): 53-bit uniform of words 0, 1
+ * Uniforms: ((w0 >> 5) 2^26 + (w1 >> 6)) 2^-53; Box-Muller r = sqrt(-2 log(1 - u1)),
+ * angle 2 pi u2, with the logarithm and sine / cosine evaluated by fixed series in
+ * correctly rounded FP64 operations, so the draws are reproducible bit for bit by any
+ * implementation that performs the same operations.  seed < 2^32, traj_index < 2^30
+ * (else LQ_ERR_ARG).  p_out (canonical [V][4][8], host or device, may be NULL) receives
+ * the final momenta.  Nothing is copied from the host.  Synchronises. */
+lq_status lq_hmc_trajectory_seeded(lq_ctx* ctx, const lq_hmc_params* params, uint64_t seed, uint64_t traj_index,
+                                   double* p_out, lq_traj_result* result);
+
+/* The heat-bath draws of lq_hmc_trajectory_seeded for (seed, traj_index), written to the
+ * caller's buffers: p momenta (canonical [V][4][8]), chi noise (canonical spinor), u the
+ * Metropolis uniform (host); any may be NULL; p and chi host or device.  Synchronises when
+ * a host buffer is written.  Errors: LQ_ERR_ARG. */
+lq_status lq_heatbath_draw(lq_ctx* ctx, uint64_t seed, uint64_t traj_index, double* p, double* chi, double* u);
+
+/* Philox4x32-10 on the device: for i < n, out[i][0..3] = the generator's four output
+ * words for counter in[i][0..3] and key in[i][4..5] (the heat bath's generator, exposed
+ * for its known-answer tests).  in, out: device buffers of uint32.  Asynchronous. */
+lq_status lq_philox4x32_10(lq_ctx* ctx, const uint32_t* in, uint32_t* out, int n);
+
 /* Measurement: apply M (dagger = 0) or M^dag (1) `n` times in precision
  * `prec` to `in` (packed once, outside the timed region) and return the
  * average device time of one application in *ms, measured with CUDA events
@@ -317,12 +370,25 @@ lq_status lq_time_dslash(lq_ctx* ctx, const double* in, double kappa, int dagger
  * same stream are ordered and safe.  Every call overwrites the whole part
  * of the array it uses before reading it, so no state carries over.
  * The first call on each device looks up the array's device address (one
- * cudaGetSymbolAddress with that device current); make that first call
- * before capturing the stream into a CUDA graph.
- * Errors: LQ_ERR_ARG, LQ_ERR_SHAPE, LQ_ERR_CUDA; the message is returned by
- * lq_last_error(NULL). */
+ * cudaGetSymbolAddress with that device current) and keeps it for the life
+ * of the process; make that first call before capturing the stream into a
+ * CUDA graph.  Calls after a device reset (cudaDeviceReset, or a reset of
+ * the primary context) are not supported: the address kept belongs to the
+ * module instance the reset unloaded.
+ * Errors: LQ_ERR_ARG (null or misaligned buffer, or a buffer that is not
+ * device memory: host buffers are refused, never read by a kernel),
+ * LQ_ERR_SHAPE (an extent < 2, or more sites than the array holds),
+ * LQ_ERR_CUDA; the message is returned by lq_last_error(NULL). */
 lq_status lq_apply_MdagM_static(double* out, const double* U, const double* in, const int dims[4],
                                 int t_antiperiodic, double kappa, void* cuda_stream);
+
+/* Measurement: the fused multiply-add rate of this GPU in *tflops (TFLOP/s, 2 flop per
+ * multiply-add) for prec = LQ_F64 or LQ_F32: eight independent multiply-add chains per
+ * thread, four blocks of 256 threads per SM, best of five launches timed with CUDA events
+ * on the context's stream.  The FP64 operator is bound by this rate rather than by HBM
+ * bandwidth on this part, so it is the denominator of the FP64 operator's roofline
+ * (the paper's FP64 kernels, Sec. 3, are here limited by the FP64 pipe).  Synchronises. */
+lq_status lq_time_fma_peak(lq_ctx* ctx, int prec, double* tflops);
 
 /* Measurement: the average device time in *ms of one CG iteration (which = 0)
  * or of one of its three passes (1: t = M p with |t|^2; 2: r -= alpha M^dag t,

@@ -56,3 +56,23 @@ def apply_MdagM(U, psi, dims, kappa, t_antiperiodic=True, nbr=None):
     nbr = nbr if nbr is not None else neighbours(dims, t_antiperiodic)
     t = apply_M(U, psi, dims, kappa, t_antiperiodic, False, None, nbr)
     return apply_M(U, t, dims, kappa, t_antiperiodic, True, None, nbr)
+
+
+def apply_MdagM_sites(U, psi, dims, kappa, sites, t_antiperiodic=True):
+    """(M^dag M psi) at ``sites`` only, shape (n, 4, 3).
+
+    M^dag M psi at x needs M psi at x and at its eight neighbours, and those need
+    psi up to two hops away.  M psi is evaluated on that one-hop neighbourhood
+    only (by ``apply_M`` with ``sites``), placed in an otherwise zero field, and
+    M^dag is applied to it at ``sites``: the same numbers as the full-lattice
+    ``apply_MdagM`` at those sites, at a cost that grows with the sample, not
+    with the lattice.
+    """
+    nbr = neighbours(dims, t_antiperiodic)
+    fwd, bwd = nbr[0], nbr[1]
+    sites = np.asarray(sites)
+    ring = np.unique(np.concatenate([sites] + [fwd[mu][sites] for mu in range(4)] +
+                                    [bwd[mu][sites] for mu in range(4)]))
+    t = np.zeros_like(psi)
+    t[ring] = apply_M(U, psi, dims, kappa, t_antiperiodic, False, ring, nbr)
+    return apply_M(U, t, dims, kappa, t_antiperiodic, True, sites, nbr)

@@ -140,7 +140,7 @@ lq_status run_chunk(lq_ctx* c, int inner, int n, double kappa) {
     LQ_CUDA(c, cudaGetLastError());
     return LQ_OK;
   }
-  auto key = std::make_tuple(c->pair_sites, inner, n, kappa);
+  auto key = std::make_tuple(c->pair_sites + 2 * c->staged, inner, n, kappa);
   auto it = c->graphs.find(key);
   if (it == c->graphs.end()) {
     cudaGraph_t graph = nullptr;
@@ -439,6 +439,99 @@ lq_status read_scalars(lq_ctx* c) {
   return LQ_OK;
 }
 
+lq_status check_trajectory_args(lq_ctx* c, const lq_hmc_params* hp, lq_traj_result* out) {
+  if (!hp || !out) return fail(c, LQ_ERR_ARG, "null parameters or result");
+  if (hp->n_steps <= 0 || !(hp->tau > 0.0) || !(hp->tol > 0.0) || hp->maxiter <= 0 || hp->reliable_every < 0)
+    return fail(c, LQ_ERR_ARG, "bad trajectory parameters");
+  LQ_TRY(check_inner(c, hp->inner_prec));
+  LQ_TRY(require_gauge(c, LQ_F64));
+  LQ_TRY(ensure_md_fields(c));
+  LQ_TRY(ensure_solver_fields(c, hp->inner_prec));
+  return LQ_OK;
+}
+
+// The trajectory after its heat bath (Eq. 5; Sec. 2; Sec. 3 steps 1-3): c->mom holds the
+// start momenta, c->chi64 the noise, u the Metropolis uniform.  p, when not null, receives
+// the final momenta.
+lq_status trajectory_after_heatbath(lq_ctx* c, const lq_hmc_params* hp, double u, double* p, lq_traj_result* out,
+                                    std::chrono::steady_clock::time_point t0, int heatbath_launches) {
+  lq_traj_result r{};
+  const Geom& g = c->geo;
+  // phi = M^dag chi; keep the start momenta and links
+  LQ_CUDA(c, cudaMemcpyAsync(c->mom0, c->mom, sizeof(double) * 32 * (size_t)g.V, cudaMemcpyDeviceToDevice,
+                             c->stream));
+  apply_M_prec(g, LQ_F64, c->gauge64, c->chi64.ref(), c->phi64.ref(), hp->kappa, true, c->stream);
+  LQ_CUDA(c, cudaMemcpyAsync(c->gauge_old, c->gauge64, gauge_bytes(GStore::F64_18, g.V), cudaMemcpyDeviceToDevice,
+                             c->stream));
+  r.kernel_launches += heatbath_launches + 1;
+  // leapfrog: half step in p, then n x (full step in U, full step in p), last p step halved
+  PhaseTimer tm(c->stream);
+  const double eps = hp->tau / hp->n_steps;
+  lq_status st = md_force_step(c, hp, 0.5 * eps, &r, tm);
+  for (int i = 0; i < hp->n_steps && st == LQ_OK; ++i) {
+    tm.begin(PhaseTimer::kLink);
+    launch_link_update(g, c->gauge64, c->mom, eps, c->stream);
+    tm.end(PhaseTimer::kLink);
+    gauge_changed(c);
+    r.kernel_launches += 1;
+    st = md_force_step(c, hp, i < hp->n_steps - 1 ? eps : 0.5 * eps, &r, tm);
+  }
+  if (st == LQ_OK) {
+    // S_f at the end: X = (M^dag M)^{-1} phi on the new links
+    lq_solve_stats s{};
+    tm.begin(PhaseTimer::kSolve);
+    st = solve_internal(c, hp->kappa, hp->tol, hp->maxiter, hp->inner_prec, hp->reliable_every, nullptr, 0, &s);
+    tm.end(PhaseTimer::kSolve);
+    r.solves += 1;
+    r.cg_iterations += s.iterations;
+    r.kernel_launches += s.kernel_launches;
+  }
+  if (st != LQ_OK) {
+    // leave the links as they were before the trajectory
+    cudaMemcpyAsync(c->gauge64, c->gauge_old, gauge_bytes(GStore::F64_18, g.V), cudaMemcpyDeviceToDevice, c->stream);
+    gauge_changed(c);
+    cudaStreamSynchronize(c->stream);
+    return st;
+  }
+  // Delta H from per-site differences
+  launch_fermion_action_diff(g, c->phi64.ref(), c->x64.ref(), c->chi64.ref(), c->rs, c->dscalar + 0, c->stream);
+  launch_kinetic_diff(g, c->mom, c->mom0, c->rs, c->dscalar + 1, c->stream);
+  launch_plaquette(g, c->gauge_old, c->gauge64, c->rs, c->dscalar + 2, c->stream);
+  r.kernel_launches += 3;
+  LQ_CUDA(c, cudaGetLastError());
+  LQ_TRY(read_scalars(c));
+  r.dSf = c->dscalar_host[0];
+  r.dK = c->dscalar_host[1];
+  r.dSg = hp->beta / 3.0 * c->dscalar_host[3];       // sum (ReTr P_old - ReTr P_new)
+  r.dH = r.dK + r.dSg + r.dSf;
+  if (!std::isfinite(r.dH)) {
+    cudaMemcpyAsync(c->gauge64, c->gauge_old, gauge_bytes(GStore::F64_18, g.V), cudaMemcpyDeviceToDevice, c->stream);
+    gauge_changed(c);
+    cudaStreamSynchronize(c->stream);
+    *out = r;
+    return fail(c, LQ_ERR_NAN, "non-finite Delta H; trajectory rejected");
+  }
+  r.accepted = (r.dH <= 0.0 || u < std::exp(-r.dH)) ? 1 : 0;
+  if (!r.accepted) {
+    LQ_CUDA(c, cudaMemcpyAsync(c->gauge64, c->gauge_old, gauge_bytes(GStore::F64_18, g.V),
+                               cudaMemcpyDeviceToDevice, c->stream));
+    gauge_changed(c);
+  }
+  launch_plaquette(g, c->gauge64, nullptr, c->rs, c->dscalar + 4, c->stream);
+  r.kernel_launches += 1;
+  LQ_TRY(read_scalars(c));
+  r.plaquette = c->dscalar_host[4] / (18.0 * g.V);
+  if (p) LQ_TRY(deliver_mom(c, c->mom, p));
+  LQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  r.seconds_solve = tm.seconds(PhaseTimer::kSolve);
+  r.seconds_gauge_force = tm.seconds(PhaseTimer::kGauge);
+  r.seconds_fermion_force = tm.seconds(PhaseTimer::kFermion);
+  r.seconds_link_update = tm.seconds(PhaseTimer::kLink);
+  *out = r;
+  return LQ_OK;
+}
+
 }  // namespace
 
 // Error text of calls that run without a context (read with lq_last_error(NULL)).
@@ -451,12 +544,14 @@ const char* lq_version(void) { return "lq 0.1 (sm_103a)"; }
 lq_status lq_create(lq_ctx** out, const int dims[4], int t_antiperiodic, void* cuda_stream) {
   if (!out || !dims) return fail(nullptr, LQ_ERR_ARG, "null argument");
   *out = nullptr;
+  // the product is checked against the limit factor by factor, so it cannot overflow
+  constexpr long long kMaxSites = (1LL << 31) / 64;
   long long V = 1;
   for (int m = 0; m < 4; ++m) {
     if (dims[m] < 2) return fail(nullptr, LQ_ERR_SHAPE, "every lattice extent must be >= 2");
+    if (dims[m] >= kMaxSites || V * dims[m] >= kMaxSites) return fail(nullptr, LQ_ERR_SHAPE, "lattice volume too large");
     V *= dims[m];
   }
-  if (V >= (1LL << 31) / 64) return fail(nullptr, LQ_ERR_SHAPE, "lattice volume too large");
   lq_ctx* c = new lq_ctx();
   c->geo.V = (int)V;
   for (int m = 0; m < 4; ++m) c->geo.L[m] = dims[m];
@@ -545,6 +640,12 @@ lq_status lq_set_option(lq_ctx* c, int option, int value) {
     case LQ_OPT_CUDA_GRAPHS: c->use_graphs = value ? 1 : 0; return LQ_OK;
     case LQ_OPT_DF64_UPDATES: c->df_updates = value ? 1 : 0; return LQ_OK;
     case LQ_OPT_PAIR_SITES: c->pair_sites = value ? 1 : 0; return LQ_OK;
+    case LQ_OPT_STAGED: c->staged = value ? 1 : 0; return LQ_OK;
+    case LQ_OPT_BATCH_RHS_PER_THREAD:
+      if (value < 0 || value > 4) return fail(c, LQ_ERR_ARG, "right-hand sides per thread must be 0 (tuned) or 1..4");
+      c->batch_rb = value;
+      if (c->batch) { destroy_batch_work(c->batch); c->batch = nullptr; }
+      return LQ_OK;
     default: return fail(c, LQ_ERR_ARG, "unknown option");
   }
 }
@@ -601,7 +702,7 @@ lq_status lq_apply_M(lq_ctx* c, double* out, const double* in, double kappa, int
   LQ_TRY(stage_spinor_in(c, in, &din));
   launch_pack_spinor(c->geo, din, s, fin.ref(), c->stream);
   const void* gauge = prec == LQ_F64 ? c->gauge64 : c->gauge_lo[prec];
-  apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites);
+  apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites, c->staged);
   LQ_CUDA(c, cudaGetLastError());
   return deliver_spinor(c, fout, out);
 }
@@ -622,8 +723,8 @@ lq_status lq_apply_MdagM(lq_ctx* c, double* out, const double* in, double kappa,
   LQ_TRY(stage_spinor_in(c, in, &din));
   launch_pack_spinor(c->geo, din, s, fin.ref(), c->stream);
   const void* gauge = prec == LQ_F64 ? c->gauge64 : c->gauge_lo[prec];
-  apply_M_prec(c->geo, prec, gauge, fin.ref(), fmid.ref(), kappa, false, c->stream, c->pair_sites);
-  apply_M_prec(c->geo, prec, gauge, fmid.ref(), fout.ref(), kappa, true, c->stream, c->pair_sites);
+  apply_M_prec(c->geo, prec, gauge, fin.ref(), fmid.ref(), kappa, false, c->stream, c->pair_sites, c->staged);
+  apply_M_prec(c->geo, prec, gauge, fmid.ref(), fout.ref(), kappa, true, c->stream, c->pair_sites, c->staged);
   LQ_CUDA(c, cudaGetLastError());
   return deliver_spinor(c, fout, out);
 }
@@ -683,14 +784,14 @@ lq_status lq_time_dslash(lq_ctx* c, const double* in, double kappa, int dagger, 
   cudaEvent_t e0, e1;
   LQ_CUDA(c, cudaEventCreate(&e0));
   LQ_CUDA(c, cudaEventCreate(&e1));
-  apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites);   // warm-up
+  apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites, c->staged);   // warm-up
   double total = 0.0;
   lq_status st = LQ_OK;
   if (flush_l2) {
     for (int i = 0; i < n && st == LQ_OK; ++i) {
       cudaMemsetAsync(flush, i & 0xff, flush_bytes, c->stream);
       cudaEventRecord(e0, c->stream);
-      apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites);
+      apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites, c->staged);
       cudaEventRecord(e1, c->stream);
       st = cuda_check(c, cudaEventSynchronize(e1), "cudaEventSynchronize");
       float t = 0.f;
@@ -700,7 +801,7 @@ lq_status lq_time_dslash(lq_ctx* c, const double* in, double kappa, int dagger, 
   } else {
     cudaEventRecord(e0, c->stream);
     for (int i = 0; i < n; ++i)
-      apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites);
+      apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites, c->staged);
     cudaEventRecord(e1, c->stream);
     st = cuda_check(c, cudaEventSynchronize(e1), "cudaEventSynchronize");
     float t = 0.f;
@@ -822,91 +923,59 @@ lq_status lq_hmc_trajectory(lq_ctx* c, const lq_hmc_params* hp, double* p, const
                             lq_traj_result* out) {
   const auto t0 = std::chrono::steady_clock::now();
   if (!c) return LQ_ERR_ARG;
-  if (!hp || !out) return fail(c, LQ_ERR_ARG, "null parameters or result");
-  if (hp->n_steps <= 0 || !(hp->tau > 0.0) || !(hp->tol > 0.0) || hp->maxiter <= 0 || hp->reliable_every < 0)
-    return fail(c, LQ_ERR_ARG, "bad trajectory parameters");
-  LQ_TRY(check_inner(c, hp->inner_prec));
-  LQ_TRY(require_gauge(c, LQ_F64));
-  LQ_TRY(ensure_md_fields(c));
-  LQ_TRY(ensure_solver_fields(c, hp->inner_prec));
-  lq_traj_result r{};
-  const Geom& g = c->geo;
-  // heat bath inputs: p (momenta) and chi; phi = M^dag chi
+  LQ_TRY(check_trajectory_args(c, hp, out));
+  // heat bath inputs from the caller: p (momenta) and chi
   LQ_TRY(stage_mom_in(c, p, c->mom));
-  LQ_CUDA(c, cudaMemcpyAsync(c->mom0, c->mom, sizeof(double) * 32 * (size_t)g.V, cudaMemcpyDeviceToDevice,
-                             c->stream));
   const double* dchi = nullptr;
   LQ_TRY(stage_spinor_in(c, chi, &dchi));
-  launch_pack_spinor(g, dchi, SStore::F64, c->chi64.ref(), c->stream);
-  apply_M_prec(g, LQ_F64, c->gauge64, c->chi64.ref(), c->phi64.ref(), hp->kappa, true, c->stream);
-  LQ_CUDA(c, cudaMemcpyAsync(c->gauge_old, c->gauge64, gauge_bytes(GStore::F64_18, g.V), cudaMemcpyDeviceToDevice,
-                             c->stream));
-  r.kernel_launches += 4;
-  // leapfrog: half step in p, then n x (full step in U, full step in p), last p step halved
-  PhaseTimer tm(c->stream);
-  const double eps = hp->tau / hp->n_steps;
-  lq_status st = md_force_step(c, hp, 0.5 * eps, &r, tm);
-  for (int i = 0; i < hp->n_steps && st == LQ_OK; ++i) {
-    tm.begin(PhaseTimer::kLink);
-    launch_link_update(g, c->gauge64, c->mom, eps, c->stream);
-    tm.end(PhaseTimer::kLink);
-    gauge_changed(c);
-    r.kernel_launches += 1;
-    st = md_force_step(c, hp, i < hp->n_steps - 1 ? eps : 0.5 * eps, &r, tm);
-  }
-  if (st == LQ_OK) {
-    // S_f at the end: X = (M^dag M)^{-1} phi on the new links
-    lq_solve_stats s{};
-    tm.begin(PhaseTimer::kSolve);
-    st = solve_internal(c, hp->kappa, hp->tol, hp->maxiter, hp->inner_prec, hp->reliable_every, nullptr, 0, &s);
-    tm.end(PhaseTimer::kSolve);
-    r.solves += 1;
-    r.cg_iterations += s.iterations;
-    r.kernel_launches += s.kernel_launches;
-  }
-  if (st != LQ_OK) {
-    // leave the links as they were before the trajectory
-    cudaMemcpyAsync(c->gauge64, c->gauge_old, gauge_bytes(GStore::F64_18, g.V), cudaMemcpyDeviceToDevice, c->stream);
-    gauge_changed(c);
-    cudaStreamSynchronize(c->stream);
-    return st;
-  }
-  // Delta H from per-site differences
-  launch_fermion_action_diff(g, c->phi64.ref(), c->x64.ref(), c->chi64.ref(), c->rs, c->dscalar + 0, c->stream);
-  launch_kinetic_diff(g, c->mom, c->mom0, c->rs, c->dscalar + 1, c->stream);
-  launch_plaquette(g, c->gauge_old, c->gauge64, c->rs, c->dscalar + 2, c->stream);
-  r.kernel_launches += 3;
+  launch_pack_spinor(c->geo, dchi, SStore::F64, c->chi64.ref(), c->stream);
+  return trajectory_after_heatbath(c, hp, u, p, out, t0, 2);
+}
+
+lq_status lq_hmc_trajectory_seeded(lq_ctx* c, const lq_hmc_params* hp, uint64_t seed, uint64_t traj_index,
+                                   double* p_out, lq_traj_result* out) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!c) return LQ_ERR_ARG;
+  if (!heatbath_counters_ok(seed, traj_index))
+    return fail(c, LQ_ERR_ARG, "seed must fit in 32 bits and traj_index be below 2^30");
+  LQ_TRY(check_trajectory_args(c, hp, out));
+  // heat bath on the device: momenta and chi from their generator streams, u on the host
+  launch_heatbath_momenta(c->geo, seed, traj_index, c->mom, nullptr, c->stream);
+  launch_heatbath_chi(c->geo, seed, traj_index, c->chi64.ref(), nullptr, c->stream);
   LQ_CUDA(c, cudaGetLastError());
-  LQ_TRY(read_scalars(c));
-  r.dSf = c->dscalar_host[0];
-  r.dK = c->dscalar_host[1];
-  r.dSg = hp->beta / 3.0 * c->dscalar_host[3];       // sum (ReTr P_old - ReTr P_new)
-  r.dH = r.dK + r.dSg + r.dSf;
-  if (!std::isfinite(r.dH)) {
-    cudaMemcpyAsync(c->gauge64, c->gauge_old, gauge_bytes(GStore::F64_18, g.V), cudaMemcpyDeviceToDevice, c->stream);
-    gauge_changed(c);
-    cudaStreamSynchronize(c->stream);
-    *out = r;
-    return fail(c, LQ_ERR_NAN, "non-finite Delta H; trajectory rejected");
+  return trajectory_after_heatbath(c, hp, metropolis_uniform(seed, traj_index), p_out, out, t0, 2);
+}
+
+lq_status lq_heatbath_draw(lq_ctx* c, uint64_t seed, uint64_t traj_index, double* p, double* chi, double* u) {
+  if (!c) return LQ_ERR_ARG;
+  if (!heatbath_counters_ok(seed, traj_index))
+    return fail(c, LQ_ERR_ARG, "seed must fit in 32 bits and traj_index be below 2^30");
+  for (const void* b : {(const void*)p, (const void*)chi})
+    if (b && !aligned16(b)) return fail(c, LQ_ERR_ARG, "buffer not 16-byte aligned");
+  if (p) {
+    if (is_device_ptr(p)) {
+      launch_heatbath_momenta(c->geo, seed, traj_index, nullptr, p, c->stream);
+    } else {
+      LQ_TRY(ensure_md_fields(c));
+      launch_heatbath_momenta(c->geo, seed, traj_index, c->mom, nullptr, c->stream);
+      LQ_CUDA(c, cudaGetLastError());
+      LQ_TRY(deliver_mom(c, c->mom, p));
+    }
+    LQ_CUDA(c, cudaGetLastError());
   }
-  r.accepted = (r.dH <= 0.0 || u < std::exp(-r.dH)) ? 1 : 0;
-  if (!r.accepted) {
-    LQ_CUDA(c, cudaMemcpyAsync(c->gauge64, c->gauge_old, gauge_bytes(GStore::F64_18, g.V),
-                               cudaMemcpyDeviceToDevice, c->stream));
-    gauge_changed(c);
+  if (chi) {
+    if (is_device_ptr(chi)) {
+      launch_heatbath_chi(c->geo, seed, traj_index, SpinorRef{nullptr, nullptr}, chi, c->stream);
+    } else {
+      launch_heatbath_chi(c->geo, seed, traj_index, SpinorRef{nullptr, nullptr}, c->stage_out, c->stream);
+      LQ_CUDA(c, cudaGetLastError());
+      LQ_CUDA(c, cudaMemcpyAsync(chi, c->stage_out, sizeof(double) * 24 * c->geo.V, cudaMemcpyDeviceToHost,
+                                 c->stream));
+      LQ_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    LQ_CUDA(c, cudaGetLastError());
   }
-  launch_plaquette(g, c->gauge64, nullptr, c->rs, c->dscalar + 4, c->stream);
-  r.kernel_launches += 1;
-  LQ_TRY(read_scalars(c));
-  r.plaquette = c->dscalar_host[4] / (18.0 * g.V);
-  LQ_TRY(deliver_mom(c, c->mom, p));
-  LQ_CUDA(c, cudaStreamSynchronize(c->stream));
-  r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  r.seconds_solve = tm.seconds(PhaseTimer::kSolve);
-  r.seconds_gauge_force = tm.seconds(PhaseTimer::kGauge);
-  r.seconds_fermion_force = tm.seconds(PhaseTimer::kFermion);
-  r.seconds_link_update = tm.seconds(PhaseTimer::kLink);
-  *out = r;
+  if (u) *u = metropolis_uniform(seed, traj_index);
   return LQ_OK;
 }
 

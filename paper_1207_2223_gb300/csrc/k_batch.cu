@@ -1,23 +1,32 @@
 // Batched CG on M^dag M: many right-hand sides sharing one gauge field, and
-// independent lattices of different volumes and kappa, solved together in
+// independent lattices of different volumes and kappa, solved together with
 // one launch per CG pass (the paper's CG routine, Sec. 3, over a batch of
 // systems).
 //
-// Layout.  All systems share one set of fields of `total` elements; system
-// k owns elements off_k .. off_k + V_k R_k - 1, its right-hand sides
-// interleaved fastest (element off_k + site * R_k + r), so the threads of one
-// site read the same link and the load is broadcast across the R_k lanes.
-// Every field is [chunk][element] as in lq_device.cuh.
+// Layout.  All systems share one set of fields of `total` elements; column r
+// (right-hand side r) of system k owns elements off_k + r V_k .. off_k +
+// (r + 1) V_k - 1, so consecutive threads read consecutive sites of one
+// column and every load is coalesced.  Every field is [chunk][element] as in
+// lq_device.cuh.  The caller's [nrhs][V][4][3] buffers map onto it directly.
 //
-// Launch.  Blocks walk a list of tiles (tile t of system k covers elements
-// (t - tile0_k) * tile .. + tile - 1 of that system); the tile size is a
-// multiple of every R_k, so a thread's right-hand side is fixed by its lane.
-// Each block accumulates per-column sums (column = system x right-hand side)
-// in shared memory tile by tile, in a fixed order; the last block adds the
-// per-block partials column by column: deterministic.
+// Work items.  A thread applies the stencil at one site to RB right-hand
+// sides of its system at once (register blocking): each link is loaded and
+// decoded (and, for 12-real storage, rebuilt) once and multiplied into RB
+// half spinors.  Blocks walk a list of tiles: tile t of system k covers the
+// sites (t - tile0_k mod tpg_k) * TILE .. + TILE - 1 of rhs group
+// (t - tile0_k) / tpg_k; a tile never spans two groups or systems, so the
+// columns a thread reduces into are the same for the whole tile.  Per-column
+// sums stay in registers while a block remains in one group, are reduced in
+// the block when it changes (fixed order) and per block are added by the
+// last block in block order: deterministic.
 //
-// Mixed precision.  The iterations run in FP32 (FP32 or 12-real FP32 links);
-// every `reliable_every` iterations x is folded into FP64 and the FP64 true
+// Tuning.  The first call on a workspace times a few iterations for every
+// candidate (threads per block x right-hand sides per thread x resident
+// blocks per SM, i.e. how many sites each thread walks) and keeps the fastest.
+//
+// Mixed precision.  The iterations run in FP32 arithmetic on the storage of
+// the inner precision; every `reliable_every` iterations (sooner for a column
+// whose iterated residual fell far) x is folded into FP64 and the FP64 true
 // residual of every column is recomputed; a column whose true residual meets
 // the tolerance is frozen (alpha = 0 from then on).
 #include <algorithm>
@@ -26,298 +35,17 @@
 #include <cstring>
 #include <vector>
 
-#include "lq_internal.h"
+#include "lq_batch.cuh"
 
 namespace lq {
-
-constexpr int kMaxSys = 16;
-constexpr int kMaxCols = 64;
-
-struct SysDesc {
-  Geom geo;
-  const void* gauge_lo;   // inner-format links of the system (SoA, stride V)
-  const void* gauge64;    // FP64 links
-  double kappa;
-  int R;                  // right-hand sides
-  int off;                // first element in the batch fields
-  int col;                // first reduction column
-  int tile0;              // first tile
-  const double* phi_in;   // canonical [R][V][4][3] complex (device)
-  double* x_out;          // canonical [R][V][4][3] complex (device)
-};
-
-struct BatchDesc {
-  int nsys, total, ncols, tile, ntiles;
-  SysDesc sys[kMaxSys];
-};
-
-// Per-column solver scalars (device).
-struct BatchState {
-  double rr[kMaxCols], rr_prev[kMaxCols], alpha[kMaxCols], beta[kMaxCols], phi2[kMaxCols], rr_true[kMaxCols];
-  double rr_ref[kMaxCols];   // |r|^2 right after the column's last reliable update
-  int done[kMaxCols];
-  int conv_iter[kMaxCols];
-  double stop2;            // tol^2
-  double delta2;           // reliable update once a column's |r|^2 fell below delta2 * rr_ref
-  int iter, iter_since_ru, ru_every, maxiter, halt, breakdown, hist_len, pad_;
-  double* hist;            // [ncols][hist_len] relative iterated residuals
-};
-
-struct BatchReduce {
-  double* partials;        // [kMaxCols][max_blocks]
-  unsigned int* ticket;
-  int max_blocks;
-};
-
-__device__ __forceinline__ int system_of_tile(const BatchDesc& bd, int t) {
-  int k = 0;
-  while (k + 1 < bd.nsys && t >= bd.sys[k + 1].tile0) ++k;
-  return k;
-}
-
-// Column sums of one block (sh_col[ncols]) -> partials; the last block adds
-// them up per column and calls fin(col_totals) in thread 0.
-template <class Fin>
-__device__ void batch_grid_sum(const BatchDesc& bd, double* sh_col, const BatchReduce& br, const Fin& fin) {
-  __shared__ bool last;
-  __syncthreads();
-  for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x)
-    br.partials[(size_t)c * br.max_blocks + blockIdx.x] = sh_col[c];
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(br.ticket, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  __shared__ double tot[kMaxCols];
-  for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) {
-    double a = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) a += __ldcg(br.partials + (size_t)c * br.max_blocks + b);
-    tot[c] = a;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    fin(tot);
-    *br.ticket = 0u;
-  }
-}
-
-// Adds one tile's per-thread values v into sh_col, per column, in a fixed order.
-__device__ __forceinline__ void tile_columns(const SysDesc& sd, double v, double* sh_tile, double* sh_col) {
-  sh_tile[threadIdx.x] = v;
-  __syncthreads();
-  if (threadIdx.x < sd.R) {
-    double a = 0.0;
-    for (int j = threadIdx.x; j < (int)blockDim.x; j += sd.R) a += sh_tile[j];
-    sh_col[sd.col + threadIdx.x] += a;
-  }
-  __syncthreads();
-}
-
-// ------------------------------------------------------------ epilogues
-// Each gets the element index e (in the batch fields), its column, the
-// result v = M in (or M^dag in) of that element, and returns the value to
-// be summed for its column.
-struct BEpiStore64 {                        // tmp = M x (FP64)
-  SpinorRef out;
-  int total;
-  __device__ bool halted() const { return false; }
-  template <typename T> __device__ double apply(int e, int, const cplx<T> v[12]) const {
-    store_spinor<SStore::F64, T>(out, total, e, v);
-    return 0.0;
-  }
-  static constexpr bool REDUCE = false;
-  __device__ void finalize(const double*) const {}
-};
-
-template <SStore S>
-struct BEpiCG1 {                             // t = M p, tt = |t|^2, alpha = rr / tt
-  SpinorRef t;
-  int total;
-  BatchState* st;
-  static constexpr bool REDUCE = true;
-  __device__ bool halted() const { return *(volatile const int*)&st->halt; }
-  template <typename T> __device__ double apply(int e, int, const cplx<T> v[12]) const {
-    store_spinor<S, T>(t, total, e, v);
-    T a = (T)0;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) { a = fma(v[k].re, v[k].re, a); a = fma(v[k].im, v[k].im, a); }
-    return (double)a;
-  }
-  __device__ void finalize_cols(const double* tot, int ncols) const {
-    for (int c = 0; c < ncols; ++c) {
-      if (st->done[c]) { st->alpha[c] = 0.0; continue; }
-      const double tt = tot[c];
-      if (!(tt > 0.0) || !isfinite(tt)) { st->breakdown = 1; st->halt = 1; st->alpha[c] = 0.0; }
-      else st->alpha[c] = st->rr[c] / tt;
-    }
-  }
-};
-
-template <SStore S>
-struct BEpiCG2 {                             // r -= alpha M^dag t, x += alpha p, rr = |r|^2
-  SpinorRef r, x, p;
-  int total;
-  BatchState* st;
-  static constexpr bool REDUCE = true;
-  __device__ bool halted() const { return *(volatile const int*)&st->halt; }
-  template <typename T> __device__ double apply(int e, int col, const cplx<T> v[12]) const {
-    const T alpha = (T)st->alpha[col];
-    cplx<T> rv[12], xv[12], pv[12];
-    load_spinor<S, T, false>(r, total, e, rv);
-    load_spinor<xlo_store(S), T, false>(x, total, e, xv);
-    load_spinor<S, T>(p, total, e, pv);
-    T a = (T)0;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      rv[k].re = fma(-alpha, v[k].re, rv[k].re);
-      rv[k].im = fma(-alpha, v[k].im, rv[k].im);
-      xv[k].re = fma(alpha, pv[k].re, xv[k].re);
-      xv[k].im = fma(alpha, pv[k].im, xv[k].im);
-      a = fma(rv[k].re, rv[k].re, a);
-      a = fma(rv[k].im, rv[k].im, a);
-    }
-    store_spinor<S, T>(r, total, e, rv);
-    store_spinor<xlo_store(S), T>(x, total, e, xv);
-    return (double)a;
-  }
-  __device__ void finalize_cols(const double* tot, int ncols) const {
-    const int it = st->iter;
-    bool all_below = true;
-    for (int c = 0; c < ncols; ++c) {
-      if (st->hist && it < st->hist_len) st->hist[(size_t)c * st->hist_len + it] = sqrt(tot[c] / st->phi2[c]);
-      if (st->done[c]) { st->beta[c] = 0.0; continue; }
-      const double rr_new = tot[c];
-      if (!isfinite(rr_new)) { st->breakdown = 1; st->halt = 1; }
-      st->beta[c] = rr_new / st->rr[c];
-      st->rr_prev[c] = st->rr[c];
-      st->rr[c] = rr_new;
-      if (rr_new > st->stop2 * st->phi2[c]) all_below = false;
-      if (rr_new < st->delta2 * st->rr_ref[c]) st->halt = 1;     // fell far: reliable update due
-    }
-    st->iter = it + 1;
-    st->iter_since_ru += 1;
-    if (all_below) st->halt = 1;
-    if (st->ru_every > 0 && st->iter_since_ru >= st->ru_every) st->halt = 1;
-    if (st->iter >= st->maxiter) st->halt = 1;
-  }
-};
-
-template <SStore S>
-struct BEpiResidual {                        // r64 = phi - M^dag tmp, r_lo = r64, rr_true = |r64|^2
-  SpinorRef phi, r64, rlo;
-  int total;
-  BatchState* st;
-  static constexpr bool REDUCE = true;
-  __device__ bool halted() const { return false; }
-  template <typename T> __device__ double apply(int e, int, const cplx<T> v[12]) const {
-    cplx<double> ph[12], rv[12];
-    load_spinor<SStore::F64, double>(phi, total, e, ph);
-    double a = 0.0;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      rv[k] = {ph[k].re - (double)v[k].re, ph[k].im - (double)v[k].im};
-      a += rv[k].re * rv[k].re + rv[k].im * rv[k].im;
-    }
-    store_spinor<SStore::F64, double>(r64, total, e, rv);
-    store_spinor<S, double>(rlo, total, e, rv);
-    return a;
-  }
-  __device__ void finalize_cols(const double* tot, int ncols) const {
-    for (int c = 0; c < ncols; ++c) {
-      st->rr_true[c] = tot[c];
-      if (st->done[c]) { st->beta[c] = 0.0; continue; }
-      if (!isfinite(tot[c])) { st->breakdown = 1; continue; }
-      if (tot[c] <= st->stop2 * st->phi2[c]) {       // converged: freeze the column
-        st->done[c] = 1;
-        st->conv_iter[c] = st->iter;
-        st->beta[c] = 0.0;
-        st->alpha[c] = 0.0;
-      } else if (tot[c] > 100.0 * st->rr[c]) {
-        // the low-precision recursion drifted far below the true residual: the
-        // search direction no longer fits it, restart the column from r
-        st->beta[c] = 0.0;
-      } else {
-        st->beta[c] = tot[c] / st->rr_prev[c];
-      }
-      st->rr[c] = tot[c];
-      st->rr_ref[c] = tot[c];
-    }
-    st->iter_since_ru = 0;
-    st->halt = 0;
-  }
-};
-
-// ------------------------------------------------------------ kernels
-template <typename T, GStore G, SStore SI, bool DAG, class Epi>
-__global__ void __launch_bounds__(256) batch_dslash_kernel(BatchDesc bd, SpinorRef in, Epi epi, BatchReduce br,
-                                                           int use64) {
-  if (epi.halted()) return;
-  extern __shared__ double smem[];
-  double* sh_tile = smem;                 // [blockDim]
-  double* sh_col = smem + blockDim.x;     // [ncols]
-  for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) sh_col[c] = 0.0;
-  __syncthreads();
-  // A thread's column is fixed while the block stays inside one system (the
-  // tile is a multiple of R), so it sums in a register and the block folds
-  // the sums into sh_col only when the system changes (block-uniform).
-  int cur = -1;
-  double acc_v = 0.0;
-  for (int t = blockIdx.x; t < bd.ntiles; t += gridDim.x) {
-    const int k = system_of_tile(bd, t);
-    if constexpr (Epi::REDUCE) {
-      if (k != cur) {
-        if (cur >= 0) tile_columns(bd.sys[cur], acc_v, sh_tile, sh_col);
-        cur = k;
-        acc_v = 0.0;
-      }
-    }
-    const SysDesc& sd = bd.sys[k];
-    const int e_loc = (t - sd.tile0) * bd.tile + threadIdx.x;
-    double v = 0.0;
-    if (e_loc < sd.geo.V * sd.R) {
-      const int s = e_loc / sd.R, r = e_loc - s * sd.R;
-      int c[4];
-      site_coords(sd.geo, s, c);
-      const BatchIndex ix{bd.total, sd.off, sd.R, r};
-      const GaugeRef U{use64 ? sd.gauge64 : sd.gauge_lo};
-      cplx<T> acc[12];
-#pragma unroll
-      for (int q = 0; q < 12; ++q) acc[q] = {(T)0, (T)0};
-      hop_dir<0, DAG, G, SI, T, BatchIndex>(sd.geo, U, in, s, c, acc, ix);
-      hop_dir<1, DAG, G, SI, T, BatchIndex>(sd.geo, U, in, s, c, acc, ix);
-      hop_dir<2, DAG, G, SI, T, BatchIndex>(sd.geo, U, in, s, c, acc, ix);
-      hop_dir<3, DAG, G, SI, T, BatchIndex>(sd.geo, U, in, s, c, acc, ix);
-      cplx<T> ctr[12];
-      load_spinor<SI, T>(in, bd.total, ix(s), ctr);
-      const T kappa = (T)sd.kappa;
-#pragma unroll
-      for (int q = 0; q < 12; ++q) {
-        acc[q].re = fma(-kappa, acc[q].re, ctr[q].re);
-        acc[q].im = fma(-kappa, acc[q].im, ctr[q].im);
-      }
-      v = epi.apply(ix(s), sd.col + r, acc);
-    }
-    acc_v += v;
-  }
-  if constexpr (Epi::REDUCE) {
-    if (cur >= 0) tile_columns(bd.sys[cur], acc_v, sh_tile, sh_col);
-    auto fin = [&](const double* tot) { epi.finalize_cols(tot, bd.ncols); };
-    batch_grid_sum(bd, sh_col, br, fin);
-  }
-}
 
 // p = r + beta_col p (inner format), skipped when halted unless forced
 template <SStore S>
 __global__ void batch_xpay_kernel(BatchDesc bd, SpinorRef r, SpinorRef p, const BatchState* st, int forced) {
   if (!forced && *(volatile const int*)&st->halt) return;
-  for (int t = blockIdx.x; t < bd.ntiles; t += gridDim.x) {
-    const int k = system_of_tile(bd, t);
-    const SysDesc& sd = bd.sys[k];
-    const int e_loc = (t - sd.tile0) * bd.tile + threadIdx.x;
-    if (e_loc >= sd.geo.V * sd.R) continue;
-    const int e = sd.off + e_loc;
-    const float beta = (float)st->beta[sd.col + e_loc % sd.R];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < bd.total; e += gridDim.x * blockDim.x) {
+    const SysDesc& sd = bd.sys[system_of_element(bd, e)];
+    const float beta = (float)st->beta[sd.col + (e - sd.off) / sd.geo.V];
     cplx<float> rv[12], pv[12];
     load_spinor<S, float>(r, bd.total, e, rv);
     load_spinor<S, float, false>(p, bd.total, e, pv);
@@ -330,40 +58,62 @@ __global__ void batch_xpay_kernel(BatchDesc bd, SpinorRef r, SpinorRef p, const 
   }
 }
 
+void launch_batch_xpay(const BatchDesc& bd, SStore s, SpinorRef r, SpinorRef p, const BatchState* st, int forced,
+                       int grid, cudaStream_t stream) {
+  switch (s) {
+    case SStore::F16: batch_xpay_kernel<SStore::F16><<<grid, 256, 0, stream>>>(bd, r, p, st, forced); break;
+    case SStore::BF16: batch_xpay_kernel<SStore::BF16><<<grid, 256, 0, stream>>>(bd, r, p, st, forced); break;
+    case SStore::I16: batch_xpay_kernel<SStore::I16><<<grid, 256, 0, stream>>>(bd, r, p, st, forced); break;
+    default: batch_xpay_kernel<SStore::F32><<<grid, 256, 0, stream>>>(bd, r, p, st, forced); break;
+  }
+}
+
 // Start: phi (canonical, per system) -> phi64; x64 = 0; x_lo = 0; r_lo = p_lo = phi; phi2 per column.
-template <SStore S>
+template <SStore S, int RB>
 __global__ void batch_init_kernel(BatchDesc bd, SpinorRef phi64, SpinorRef x64, SpinorRef xlo, SpinorRef rlo,
                                   SpinorRef plo, BatchState* st, BatchReduce br) {
-  extern __shared__ double smem[];
-  double* sh_tile = smem;
-  double* sh_col = smem + blockDim.x;
+  __shared__ double sh_col[kMaxCols];
+  __shared__ double sh_red[RB * 32];
   for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) sh_col[c] = 0.0;
   __syncthreads();
+  int cur = -1;
+  double red[RB];
+#pragma unroll
+  for (int j = 0; j < RB; ++j) red[j] = 0.0;
   for (int t = blockIdx.x; t < bd.ntiles; t += gridDim.x) {
-    const int k = system_of_tile(bd, t);
-    const SysDesc& sd = bd.sys[k];
-    const int e_loc = (t - sd.tile0) * bd.tile + threadIdx.x;
-    double v = 0.0;
-    if (e_loc < sd.geo.V * sd.R) {
-      const int s = e_loc / sd.R, r = e_loc - s * sd.R;
-      const int e = sd.off + e_loc;
-      const double2* src = reinterpret_cast<const double2*>(sd.phi_in) + ((size_t)r * sd.geo.V + s) * 12;
+    const TileWork w = tile_work(bd, t);
+    const SysDesc& sd = bd.sys[w.k];
+    const int col0 = sd.col + w.r0;
+    if (col0 != cur) {
+      if (cur >= 0) flush_columns<RB>(red, cur, sh_red, sh_col);
+      cur = col0;
+#pragma unroll
+      for (int j = 0; j < RB; ++j) red[j] = 0.0;
+    }
+    if (w.s >= sd.geo.V) continue;
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      const int el = (w.r0 + j) * sd.geo.V + w.s;            // element within the system
+      const double2* src = reinterpret_cast<const double2*>(sd.phi_in) + (size_t)el * 12;
       cplx<double> a[12], z[12];
+      double v = 0.0;
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
-        const double2 w = src[q];
-        a[q] = {w.x, w.y};
+        const double2 x = src[q];
+        a[q] = {x.x, x.y};
         z[q] = {0.0, 0.0};
-        v += w.x * w.x + w.y * w.y;
+        v += x.x * x.x + x.y * x.y;
       }
+      const int e = sd.off + el;
       store_spinor<SStore::F64, double>(phi64, bd.total, e, a);
       store_spinor<SStore::F64, double>(x64, bd.total, e, z);
       store_spinor<xlo_store(S), double>(xlo, bd.total, e, z);
       store_spinor<S, double>(rlo, bd.total, e, a);
       store_spinor<S, double>(plo, bd.total, e, a);
+      red[j] += v;
     }
-    tile_columns(sd, v, sh_tile, sh_col);
   }
+  if (cur >= 0) flush_columns<RB>(red, cur, sh_red, sh_col);
   auto fin = [&](const double* tot) {
     for (int c = 0; c < bd.ncols; ++c) {
       st->phi2[c] = tot[c];
@@ -391,17 +141,13 @@ __global__ void batch_accumulate_kernel(int total, SpinorRef xlo, SpinorRef x64)
   }
 }
 
-// x64 -> canonical per system
+// x64 -> canonical per system (element off + r V + s is canonical entry r V + s of x_out)
 __global__ void batch_unpack_kernel(BatchDesc bd, SpinorRef x64) {
-  for (int t = blockIdx.x; t < bd.ntiles; t += gridDim.x) {
-    const int k = system_of_tile(bd, t);
-    const SysDesc& sd = bd.sys[k];
-    const int e_loc = (t - sd.tile0) * bd.tile + threadIdx.x;
-    if (e_loc >= sd.geo.V * sd.R) continue;
-    const int s = e_loc / sd.R, r = e_loc - s * sd.R;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < bd.total; e += gridDim.x * blockDim.x) {
+    const SysDesc& sd = bd.sys[system_of_element(bd, e)];
     cplx<double> a[12];
-    load_spinor<SStore::F64, double>(x64, bd.total, sd.off + e_loc, a);
-    double2* dst = reinterpret_cast<double2*>(sd.x_out) + ((size_t)r * sd.geo.V + s) * 12;
+    load_spinor<SStore::F64, double>(x64, bd.total, e, a);
+    double2* dst = reinterpret_cast<double2*>(sd.x_out) + (size_t)(e - sd.off) * 12;
 #pragma unroll
     for (int q = 0; q < 12; ++q) dst[q] = make_double2(a[q].re, a[q].im);
   }
@@ -410,16 +156,24 @@ __global__ void batch_unpack_kernel(BatchDesc bd, SpinorRef x64) {
 // ------------------------------------------------------------ host side
 namespace {
 
+// Launch shape of the inner-format passes, picked by timing.
+struct Tuning {
+  int tile = 0;                   // threads per block (= sites per tile)
+  int rb = 1;                     // right-hand sides per thread
+  int per_sm = 0;                 // resident blocks per SM used (0: all that fit)
+};
+
 struct BatchWork {
   std::vector<int> key;           // signature: per system dims, R, antiperiodic, precision
-  int total = 0, ncols = 0, grid_cap = 0;
+  int total = 0, ncols = 0, sms = 0, max_blocks = 0;
   Field phi64, x64, r64, tmp64, plo, tlo, rlo, xlo;
   BatchState* st = nullptr;
   BatchState* st_host = nullptr;
   BatchReduce br{};
   double* hist = nullptr;
   int hist_cap = 0;
-  int tile = 0;                   // tuned tile size
+  Tuning tune;
+  std::vector<double> tune_ms;    // timing of every candidate (for the caller's report)
   // recorded iteration graphs with the descriptor they were recorded for
   std::vector<std::pair<BatchDesc, cudaGraphExec_t>> graphs;
 };
@@ -450,10 +204,11 @@ void free_batch(BatchWork* w) {
 }
 
 BatchDesc make_desc(lq_ctx** ctxs, int n, int R, const double* const* phi, double* const* x, const double* kappa,
-                    int prec, int tile) {
+                    int prec, int tile, int rb) {
   BatchDesc bd{};
   bd.nsys = n;
   bd.tile = tile;
+  bd.rb = rb;
   int off = 0, col = 0, t0 = 0;
   for (int k = 0; k < n; ++k) {
     SysDesc& sd = bd.sys[k];
@@ -465,11 +220,12 @@ BatchDesc make_desc(lq_ctx** ctxs, int n, int R, const double* const* phi, doubl
     sd.off = off;
     sd.col = col;
     sd.tile0 = t0;
+    sd.tpg = (sd.geo.V + tile - 1) / tile;
     sd.phi_in = phi ? phi[k] : nullptr;
     sd.x_out = x ? x[k] : nullptr;
     off += sd.geo.V * R;
     col += R;
-    t0 += (sd.geo.V * R + tile - 1) / tile;
+    t0 += sd.tpg * (R / rb);
   }
   bd.total = off;
   bd.ncols = col;
@@ -477,88 +233,65 @@ BatchDesc make_desc(lq_ctx** ctxs, int n, int R, const double* const* phi, doubl
   return bd;
 }
 
-// One wave of resident blocks: a second wave would sweep the lattice again
-// after the first, losing the L2 reuse of neighbour spinors.
-template <typename T, GStore G, SStore SI, bool DAG, class Epi>
-void launch_batch(const BatchDesc& bd, SpinorRef in, const Epi& epi, const BatchReduce& br, int use64,
-                  int grid_cap, cudaStream_t st) {
-  const int wave = resident_grid(reinterpret_cast<const void*>(&batch_dslash_kernel<T, G, SI, DAG, Epi>), bd.tile);
-  const int grid = std::min(std::min(bd.ntiles, grid_cap), wave);
-  const size_t sh = sizeof(double) * (bd.tile + bd.ncols);
-  batch_dslash_kernel<T, G, SI, DAG, Epi><<<grid, bd.tile, sh, st>>>(bd, in, epi, br, use64);
+int flat_grid(const BatchWork* w) { return std::max(1, w->sms) * 8; }
+
+BatchIterArgs iter_args(const BatchWork* w, const Tuning& tu) {
+  return BatchIterArgs{w->plo.ref(), w->tlo.ref(), w->rlo.ref(), w->xlo.ref(), w->st, w->br, w->sms, tu.per_sm};
 }
 
-template <GStore G, SStore S>
-void batch_iteration(BatchWork* w, const BatchDesc& bd, cudaStream_t st) {
-  BEpiCG1<S> e1{w->tlo.ref(), bd.total, w->st};
-  launch_batch<float, G, S, false>(bd, w->plo.ref(), e1, w->br, 0, w->grid_cap, st);
-  BEpiCG2<S> e2{w->rlo.ref(), w->xlo.ref(), w->plo.ref(), bd.total, w->st};
-  launch_batch<float, G, S, true>(bd, w->tlo.ref(), e2, w->br, 0, w->grid_cap, st);
-  batch_xpay_kernel<S><<<std::min(bd.ntiles, w->grid_cap), bd.tile, 0, st>>>(bd, w->rlo.ref(), w->plo.ref(),
-                                                                             w->st, 0);
-}
-
-void batch_iteration_prec(BatchWork* w, const BatchDesc& bd, int prec, cudaStream_t st) {
+void batch_iteration_prec(BatchWork* w, const BatchDesc& bd, int prec, const Tuning& tu, cudaStream_t st) {
+  const BatchIterArgs a = iter_args(w, tu);
   switch (prec) {
-    case LQ_F32_12: batch_iteration<GStore::F32_12, SStore::F32>(w, bd, st); break;
-    case LQ_F16_12: batch_iteration<GStore::F16_12, SStore::F16>(w, bd, st); break;
-    case LQ_I16_12: batch_iteration<GStore::I16_12, SStore::I16>(w, bd, st); break;
-    default: batch_iteration<GStore::F32_18, SStore::F32>(w, bd, st); break;
+    case LQ_F16_12: case LQ_BF16_12: batch_iteration_h16(a, bd, prec, st); break;
+    case LQ_I16_12: batch_iteration_i16(a, bd, prec, st); break;
+    default: batch_iteration_f32(a, bd, prec, st); break;
   }
 }
 
 template <SStore S>
-void batch_true_residual_s(BatchWork* w, const BatchDesc& bd, cudaStream_t st) {
-  BEpiStore64 e0{w->tmp64.ref(), bd.total};
-  launch_batch<double, GStore::F64_18, SStore::F64, false>(bd, w->x64.ref(), e0, w->br, 1, w->grid_cap, st);
-  BEpiResidual<S> e1{w->phi64.ref(), w->r64.ref(), w->rlo.ref(), bd.total, w->st};
-  launch_batch<double, GStore::F64_18, SStore::F64, true>(bd, w->tmp64.ref(), e1, w->br, 1, w->grid_cap, st);
-}
-
-void batch_true_residual(BatchWork* w, const BatchDesc& bd, int prec, cudaStream_t st) {
-  switch (spinor_store_of(prec)) {
-    case SStore::F16: batch_true_residual_s<SStore::F16>(w, bd, st); break;
-    case SStore::I16: batch_true_residual_s<SStore::I16>(w, bd, st); break;
-    default: batch_true_residual_s<SStore::F32>(w, bd, st); break;
-  }
+void batch_true_residual_s(BatchWork* w, const BatchDesc& bd64, cudaStream_t st) {
+  BEpiStore64 e0{w->tmp64.ref(), bd64.total};
+  launch_batch<double, GStore::F64_18, SStore::F64, false>(bd64, w->x64.ref(), e0, w->br, 1, w->sms, 0, st);
+  BEpiResidual<S> e1{w->phi64.ref(), w->r64.ref(), w->rlo.ref(), bd64.total, w->st};
+  launch_batch<double, GStore::F64_18, SStore::F64, true>(bd64, w->tmp64.ref(), e1, w->br, 1, w->sms, 0, st);
 }
 
 // the format-dependent element kernels of the host loop
-void batch_init(BatchWork* w, const BatchDesc& bd, int prec, int grid, cudaStream_t st) {
-  const size_t sh = sizeof(double) * (bd.tile + bd.ncols);
-  switch (spinor_store_of(prec)) {
-    case SStore::F16:
-      batch_init_kernel<SStore::F16><<<grid, bd.tile, sh, st>>>(bd, w->phi64.ref(), w->x64.ref(), w->xlo.ref(),
-                                                                w->rlo.ref(), w->plo.ref(), w->st, w->br);
-      break;
-    case SStore::I16:
-      batch_init_kernel<SStore::I16><<<grid, bd.tile, sh, st>>>(bd, w->phi64.ref(), w->x64.ref(), w->xlo.ref(),
-                                                                w->rlo.ref(), w->plo.ref(), w->st, w->br);
-      break;
-    default:
-      batch_init_kernel<SStore::F32><<<grid, bd.tile, sh, st>>>(bd, w->phi64.ref(), w->x64.ref(), w->xlo.ref(),
-                                                                w->rlo.ref(), w->plo.ref(), w->st, w->br);
-      break;
+template <SStore S>
+void batch_init_s(BatchWork* w, const BatchDesc& bd, cudaStream_t st) {
+  const int grid = std::max(1, std::min(bd.ntiles, w->br.max_blocks));
+  auto args = [&](auto kern) {
+    kern<<<grid, bd.tile, 0, st>>>(bd, w->phi64.ref(), w->x64.ref(), w->xlo.ref(), w->rlo.ref(), w->plo.ref(), w->st,
+                                   w->br);
+  };
+  switch (bd.rb) {
+    case 2: args(&batch_init_kernel<S, 2>); break;
+    case 3: args(&batch_init_kernel<S, 3>); break;
+    case 4: args(&batch_init_kernel<S, 4>); break;
+    default: args(&batch_init_kernel<S, 1>); break;
   }
 }
-void batch_reliable_tail(BatchWork* w, const BatchDesc& bd, const BatchDesc& bd64, int prec, int grid,
-                         cudaStream_t st) {
+void batch_init(BatchWork* w, const BatchDesc& bd, int prec, cudaStream_t st) {
   switch (spinor_store_of(prec)) {
-    case SStore::F16:
-      batch_accumulate_kernel<SStore::F16><<<grid, bd.tile, 0, st>>>(bd.total, w->xlo.ref(), w->x64.ref());
-      batch_true_residual(w, bd64, prec, st);
-      batch_xpay_kernel<SStore::F16><<<grid, bd.tile, 0, st>>>(bd, w->rlo.ref(), w->plo.ref(), w->st, 1);
-      break;
-    case SStore::I16:
-      batch_accumulate_kernel<SStore::I16><<<grid, bd.tile, 0, st>>>(bd.total, w->xlo.ref(), w->x64.ref());
-      batch_true_residual(w, bd64, prec, st);
-      batch_xpay_kernel<SStore::I16><<<grid, bd.tile, 0, st>>>(bd, w->rlo.ref(), w->plo.ref(), w->st, 1);
-      break;
-    default:
-      batch_accumulate_kernel<SStore::F32><<<grid, bd.tile, 0, st>>>(bd.total, w->xlo.ref(), w->x64.ref());
-      batch_true_residual(w, bd64, prec, st);
-      batch_xpay_kernel<SStore::F32><<<grid, bd.tile, 0, st>>>(bd, w->rlo.ref(), w->plo.ref(), w->st, 1);
-      break;
+    case SStore::F16: batch_init_s<SStore::F16>(w, bd, st); break;
+    case SStore::BF16: batch_init_s<SStore::BF16>(w, bd, st); break;
+    case SStore::I16: batch_init_s<SStore::I16>(w, bd, st); break;
+    default: batch_init_s<SStore::F32>(w, bd, st); break;
+  }
+}
+
+template <SStore S>
+void batch_reliable_tail_s(BatchWork* w, const BatchDesc& bd, const BatchDesc& bd64, cudaStream_t st) {
+  batch_accumulate_kernel<S><<<flat_grid(w), 256, 0, st>>>(bd.total, w->xlo.ref(), w->x64.ref());
+  batch_true_residual_s<S>(w, bd64, st);
+  batch_xpay_kernel<S><<<flat_grid(w), 256, 0, st>>>(bd, w->rlo.ref(), w->plo.ref(), w->st, 1);
+}
+void batch_reliable_tail(BatchWork* w, const BatchDesc& bd, const BatchDesc& bd64, int prec, cudaStream_t st) {
+  switch (spinor_store_of(prec)) {
+    case SStore::F16: batch_reliable_tail_s<SStore::F16>(w, bd, bd64, st); break;
+    case SStore::BF16: batch_reliable_tail_s<SStore::BF16>(w, bd, bd64, st); break;
+    case SStore::I16: batch_reliable_tail_s<SStore::I16>(w, bd, bd64, st); break;
+    default: batch_reliable_tail_s<SStore::F32>(w, bd, bd64, st); break;
   }
 }
 
@@ -580,8 +313,9 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
   if (!x || !phi || !kappa) return fail(LQ_ERR_ARG, "null argument");
   if (nrhs <= 0 || nrhs > 16 || n * nrhs > kMaxCols) return fail(LQ_ERR_ARG, "need 1 <= nrhs <= 16, n * nrhs <= 64");
   if (!(tol > 0.0) || maxiter <= 0 || reliable_every <= 0) return fail(LQ_ERR_ARG, "bad tol, maxiter or reliable_every");
-  if (inner_prec != LQ_F32 && inner_prec != LQ_F32_12 && inner_prec != LQ_F16_12 && inner_prec != LQ_I16_12)
-    return fail(LQ_ERR_ARG, "inner precision must be LQ_F32, LQ_F32_12, LQ_F16_12 or LQ_I16_12");
+  if (inner_prec != LQ_F32 && inner_prec != LQ_F32_12 && inner_prec != LQ_F16_12 && inner_prec != LQ_BF16_12 &&
+      inner_prec != LQ_I16_12)
+    return fail(LQ_ERR_ARG, "inner precision must be LQ_F32, LQ_F32_12, LQ_F16_12, LQ_BF16_12 or LQ_I16_12");
   for (int k = 0; k < n; ++k) {
     if (!ctxs[k] || !ctxs[k]->gauge_set) return fail(LQ_ERR_STATE, "every context needs a gauge field");
     if (ctxs[k]->device != c->device) return fail(LQ_ERR_ARG, "all contexts must be on one device");
@@ -618,22 +352,23 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
     w = new BatchWork();
     c->batch = w;
     w->key = key;
-    BatchDesc probe = make_desc(ctxs, n, nrhs, nullptr, nullptr, kappa, inner_prec, nrhs);
+    BatchDesc probe = make_desc(ctxs, n, nrhs, nullptr, nullptr, kappa, inner_prec, 256, 1);
     w->total = probe.total;
     w->ncols = probe.ncols;
     bool ok = true;
     auto alloc = [&](Field& f, SStore s) {
       f.store = s;
       ok = ok && cudaMalloc(&f.data, spinor_bytes(s, w->total)) == cudaSuccess;
-      if (s == SStore::F16 || s == SStore::I16) ok = ok && cudaMalloc(&f.norm, sizeof(float) * w->total) == cudaSuccess;
+      if (s == SStore::F16 || s == SStore::BF16 || s == SStore::I16)
+        ok = ok && cudaMalloc(&f.norm, sizeof(float) * w->total) == cudaSuccess;
     };
     const SStore slo = spinor_store_of(inner_prec);
     alloc(w->phi64, SStore::F64); alloc(w->x64, SStore::F64); alloc(w->r64, SStore::F64); alloc(w->tmp64, SStore::F64);
     alloc(w->plo, slo); alloc(w->tlo, slo); alloc(w->rlo, slo); alloc(w->xlo, xlo_store(slo));
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    w->grid_cap = std::max(1, sms) * 4;
-    w->br.max_blocks = w->grid_cap;
+    cudaDeviceGetAttribute(&w->sms, cudaDevAttrMultiProcessorCount, c->device);
+    w->sms = std::max(1, w->sms);
+    w->max_blocks = w->sms * 8;
+    w->br.max_blocks = w->max_blocks;
     ok = ok && cudaMalloc(&w->br.partials, sizeof(double) * kMaxCols * w->br.max_blocks) == cudaSuccess;
     ok = ok && cudaMalloc(&w->br.ticket, sizeof(unsigned int)) == cudaSuccess;
     ok = ok && cudaMemset(w->br.ticket, 0, sizeof(unsigned int)) == cudaSuccess;
@@ -656,7 +391,7 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
   // state
   BatchState h{};
   h.stop2 = tol * tol;
-  h.delta2 = inner_prec == LQ_F32 || inner_prec == LQ_F32_12 ? 1e-6 : 1e-4;
+  h.delta2 = inner_prec == LQ_F32 || inner_prec == LQ_F32_12 ? 1e-6 : (inner_prec == LQ_BF16_12 ? 1e-2 : 1e-4);
   h.ru_every = reliable_every;
   h.maxiter = maxiter;
   h.hist = (hist && hist_len > 0) ? w->hist : nullptr;
@@ -665,43 +400,59 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
   cudaMemcpyAsync(w->st, w->st_host, sizeof(BatchState), cudaMemcpyHostToDevice, st);
   lq_solve_stats s{};
 
-  // autotune the tile (threads per block) once per workspace: multiples of
-  // nrhs near 128 and 256 threads, timed over three iterations each
-  const int base = nrhs;
-  if (w->tile == 0) {
-    std::vector<int> cand;
-    for (int target : {128, 256}) {
-      const int t = std::max(base, target / base * base);
-      if (t <= 256 && std::find(cand.begin(), cand.end(), t) == cand.end()) cand.push_back(t);
-    }
-    BatchDesc bd0 = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, cand[0]);
-    batch_init(w, bd0, inner_prec, std::min(bd0.ntiles, w->grid_cap), st);
+  // autotune once per workspace: threads per block {128, 256} x right-hand sides per
+  // thread {1, 2, 3, 4} (divisors of nrhs) x resident blocks per SM {all that fit, 1},
+  // each timed over three iterations on the real fields
+  if (c->batch_rb > 0 && w->tune.tile == 0) {       // fixed by the caller: no timing
+    if (nrhs % c->batch_rb != 0) return fail(LQ_ERR_ARG, "right-hand sides per thread must divide nrhs");
+    w->tune.tile = 256;
+    w->tune.rb = c->batch_rb;
+    w->tune.per_sm = 0;
+    w->tune_ms.clear();
+  }
+  if (w->tune.tile == 0) {
+    std::vector<Tuning> cand;
+    for (int rb : {1, 2, 3, 4})
+      if (nrhs % rb == 0)
+        for (int tile : {256, 128})
+          for (int per_sm : {0, 1}) {
+            if (per_sm == 1 && tile == 128) continue;
+            Tuning t;
+            t.tile = tile;
+            t.rb = rb;
+            t.per_sm = per_sm;
+            cand.push_back(t);
+          }
+    BatchDesc bd0 = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, cand[0].tile, cand[0].rb);
+    batch_init(w, bd0, inner_prec, st);
     float best = 1e30f;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    for (int t : cand) {
-      BatchDesc bd = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, t);
-      batch_iteration_prec(w, bd, inner_prec, st);   // warm-up
+    w->tune_ms.clear();
+    for (const Tuning& t : cand) {
+      BatchDesc bd = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, t.tile, t.rb);
+      batch_iteration_prec(w, bd, inner_prec, t, st);   // warm-up
       cudaEventRecord(a, st);
-      for (int i = 0; i < 3; ++i) batch_iteration_prec(w, bd, inner_prec, st);
+      for (int i = 0; i < 3; ++i) batch_iteration_prec(w, bd, inner_prec, t, st);
       cudaEventRecord(b, st);
       cudaEventSynchronize(b);
       float ms = 0.f;
       cudaEventElapsedTime(&ms, a, b);
       s.kernel_launches += 12;
-      if (ms < best) { best = ms; w->tile = t; }
+      w->tune_ms.push_back(ms / 3.0);
+      if (ms < best) { best = ms; w->tune = t; }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     *w->st_host = h;
     cudaMemcpyAsync(w->st, w->st_host, sizeof(BatchState), cudaMemcpyHostToDevice, st);
   }
-  const BatchDesc bd = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, w->tile);
-  // FP64 passes (~250 registers per thread) use tiles of about 128 threads
-  const BatchDesc bd64 = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, std::max(nrhs, 128 / nrhs * nrhs));
-  const int grid = std::min(bd.ntiles, w->grid_cap);
-  batch_init(w, bd, inner_prec, grid, st);
+  const Tuning tu = w->tune;
+  const BatchDesc bd = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, tu.tile, tu.rb);
+  // FP64 passes (~250 registers per thread): one right-hand side per thread, 128 threads
+  const BatchDesc bd64 = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, 128, 1);
+  batch_init(w, bd, inner_prec, st);
   s.kernel_launches += 1;
 
   // iterations as CUDA graphs of reliable_every iterations
@@ -716,7 +467,7 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
       cudaGraph_t g = nullptr;
       err = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
       if (err != cudaSuccess) break;
-      for (int i = 0; i < chunk; ++i) batch_iteration_prec(w, bd, inner_prec, c->capture_stream);
+      for (int i = 0; i < chunk; ++i) batch_iteration_prec(w, bd, inner_prec, tu, c->capture_stream);
       err = cudaStreamEndCapture(c->capture_stream, &g);
       if (err != cudaSuccess) break;
       err = cudaGraphInstantiate(&exec, g, 0);
@@ -734,7 +485,7 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
     if (err != cudaSuccess) break;
     s.kernel_launches += 3 * chunk;
     // reliable update: fold x, FP64 true residual per column, freeze converged columns
-    batch_reliable_tail(w, bd, bd64, inner_prec, grid, st);
+    batch_reliable_tail(w, bd, bd64, inner_prec, st);
     s.kernel_launches += 4;
     s.reliable_updates++;
     err = cudaMemcpyAsync(w->st_host, w->st, sizeof(BatchState), cudaMemcpyDeviceToHost, st);
@@ -751,7 +502,7 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
     cudaGetLastError();
     return fail(LQ_ERR_CUDA, cudaGetErrorString(err));
   }
-  batch_unpack_kernel<<<grid, bd.tile, 0, st>>>(bd, w->x64.ref());
+  batch_unpack_kernel<<<flat_grid(w), 256, 0, st>>>(bd, w->x64.ref());
   s.kernel_launches += 1;
   const BatchState& hs = *w->st_host;
   s.iterations = hs.iter;
@@ -774,4 +525,20 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
   s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats) *stats = s;
   return result;
+}
+
+extern "C" lq_status lq_batch_tuning(lq_ctx* c, int* tile, int* rhs_per_thread, int* blocks_per_sm, double* ms,
+                                     int ms_len) {
+  if (!c) return LQ_ERR_ARG;
+  const BatchWork* w = static_cast<const BatchWork*>(c->batch);
+  if (!w || w->tune.tile == 0) {
+    c->last_error = "lq_batch_tuning: no batched solve has run on this context";
+    return LQ_ERR_STATE;
+  }
+  if (tile) *tile = w->tune.tile;
+  if (rhs_per_thread) *rhs_per_thread = w->tune.rb;
+  if (blocks_per_sm) *blocks_per_sm = w->tune.per_sm;
+  if (ms)
+    for (int i = 0; i < ms_len && i < (int)w->tune_ms.size(); ++i) ms[i] = w->tune_ms[i];
+  return LQ_OK;
 }

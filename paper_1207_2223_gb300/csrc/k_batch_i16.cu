@@ -1,0 +1,10 @@
+// The batched solver's iteration for 16-bit fixed-point storage.
+#include "lq_batch.cuh"
+
+namespace lq {
+
+void batch_iteration_i16(const BatchIterArgs& a, const BatchDesc& bd, int, cudaStream_t st) {
+  batch_iteration_t<GStore::I16_12, SStore::I16>(a, bd, st);
+}
+
+}  // namespace lq

@@ -4,33 +4,36 @@
 // the 16-bit formats (xlo_store).  The FP64 solution and residual are
 // corrected by reliable updates driven from the host (api.cu).
 #include "lq_internal.h"
+#include "lq_staged.cuh"
 
 namespace lq {
 
-template <GStore G, SStore S>
-static void iteration(lq_ctx* c, const void* gauge, double kappa, cudaStream_t stream) {
-  const Geom& g = c->geo;
-  GaugeRef U{gauge};
-  const int k = (int)S;
-  EpiCG1<S> e1{c->t_lo[k].ref(), c->state};
-  launch_dslash<float, G, S, false>(g, U, c->p_lo[k].ref(), kappa, e1, c->rs, stream);
-  EpiCG2<S, xlo_store(S), S> e2{c->r_lo[k].ref(), c->x_lo[k].ref(), c->p_lo[k].ref(), c->state};
-  launch_dslash<float, G, S, true>(g, U, c->t_lo[k].ref(), kappa, e2, c->rs, stream);
-  launch_xpay_p(g, S, c->r_lo[k].ref(), c->p_lo[k].ref(), c->state, false, stream);
+// One stencil pass: the plain kernel, or the one sharing x and y links in-block (option LQ_OPT_STAGED).
+template <GStore G, SStore S, bool DAG, class Epi>
+static void pass(const lq_ctx* c, GaugeRef U, SpinorRef in, double kappa, const Epi& e, cudaStream_t stream) {
+  if (c->staged) launch_dslash_staged<float, G, S, DAG>(c->geo, U, in, kappa, e, c->rs, stream);
+  else launch_dslash<float, G, S, DAG>(c->geo, U, in, kappa, e, c->rs, stream);
 }
 
 template <GStore G, SStore S>
 static void step(lq_ctx* c, const void* gauge, int which, double kappa, cudaStream_t stream) {
-  const Geom& g = c->geo;
   GaugeRef U{gauge};
   const int k = (int)S;
   if (which == 1) {
     EpiCG1<S> e1{c->t_lo[k].ref(), c->state};
-    launch_dslash<float, G, S, false>(g, U, c->p_lo[k].ref(), kappa, e1, c->rs, stream);
+    pass<G, S, false>(c, U, c->p_lo[k].ref(), kappa, e1, stream);
   } else {
     EpiCG2<S, xlo_store(S), S> e2{c->r_lo[k].ref(), c->x_lo[k].ref(), c->p_lo[k].ref(), c->state};
-    launch_dslash<float, G, S, true>(g, U, c->t_lo[k].ref(), kappa, e2, c->rs, stream);
+    pass<G, S, true>(c, U, c->t_lo[k].ref(), kappa, e2, stream);
   }
+}
+
+template <GStore G, SStore S>
+static void iteration(lq_ctx* c, const void* gauge, double kappa, cudaStream_t stream) {
+  const int k = (int)S;
+  step<G, S>(c, gauge, 1, kappa, stream);
+  step<G, S>(c, gauge, 2, kappa, stream);
+  launch_xpay_p(c->geo, S, c->r_lo[k].ref(), c->p_lo[k].ref(), c->state, false, stream);
 }
 
 // The two-site packed passes replace the one-site ones for 16-bit fixed point

@@ -83,12 +83,27 @@ __global__ void __launch_bounds__(256) hop_canonical_kernel(Geom geo, const doub
 
 namespace {
 
+// True when p is device (or managed) memory.  cudaPointerGetAttributes
+// allocates nothing; host memory, including pinned or unregistered host
+// buffers, is refused before any kernel sees it.
+bool static_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mutex;
 double2* g_static_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once
-// per device (the first call on each device).
+// per device (the first call on each device) and kept for the life of the
+// process.  A device reset (cudaDeviceReset, or a reset of the primary
+// context) unloads the module that holds the array, so calls after one are
+// not supported.
 cudaError_t static_scratch_address(double2** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -118,23 +133,31 @@ extern "C" lq_status lq_apply_MdagM_static(double* out, const double* U, const d
     lq_set_global_error("lq_apply_MdagM_static: null argument");
     return LQ_ERR_ARG;
   }
+  // Each extent is checked before it enters the product, and the product stops
+  // growing as soon as it passes the limit, so it cannot overflow.
   long long V = 1;
   for (int m = 0; m < 4; ++m) {
     if (dims[m] < 2) {
       lq_set_global_error("lq_apply_MdagM_static: every lattice extent must be >= 2");
       return LQ_ERR_SHAPE;
     }
+    if (dims[m] > kStaticMaxSites || V * dims[m] > kStaticMaxSites) {
+      lq_set_global_error("lq_apply_MdagM_static: lattice " + std::to_string(dims[0]) + "x" +
+                          std::to_string(dims[1]) + "x" + std::to_string(dims[2]) + "x" + std::to_string(dims[3]) +
+                          " has more sites than the built-in scratch array holds (at most " +
+                          std::to_string(kStaticMaxSites) + ")");
+      return LQ_ERR_SHAPE;
+    }
     V *= dims[m];
-  }
-  if (V > kStaticMaxSites) {
-    lq_set_global_error("lq_apply_MdagM_static: lattice has " + std::to_string(V) +
-                        " sites; the built-in scratch array holds at most " + std::to_string(kStaticMaxSites));
-    return LQ_ERR_SHAPE;
   }
   const uintptr_t mis = (reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(U) |
                          reinterpret_cast<uintptr_t>(in)) & 15u;
   if (mis) {
     lq_set_global_error("lq_apply_MdagM_static: buffers must be 16-byte aligned");
+    return LQ_ERR_ARG;
+  }
+  if (!static_device_ptr(out) || !static_device_ptr(U) || !static_device_ptr(in)) {
+    lq_set_global_error("lq_apply_MdagM_static: U, in and out must be device buffers");
     return LQ_ERR_ARG;
   }
   double2* scratch = nullptr;

@@ -1,0 +1,432 @@
+// Batched CG on M^dag M (the paper's CG routine, Sec. 3, over a batch of
+// systems): descriptors, per-column solver state, epilogues and the
+// register-blocked stencil kernel shared by the translation units of the
+// batched solver (k_batch.cu drives it; k_batch_*.cu instantiate the
+// iteration for each storage format).
+#pragma once
+#include <algorithm>
+
+#include "lq_internal.h"
+
+namespace lq {
+
+constexpr int kMaxSys = 16;
+constexpr int kMaxCols = 64;
+constexpr int kMaxRB = 4;
+
+struct SysDesc {
+  Geom geo;
+  const void* gauge_lo;   // inner-format links of the system (SoA, stride V)
+  const void* gauge64;    // FP64 links
+  double kappa;
+  int R;                  // right-hand sides
+  int off;                // first element in the batch fields
+  int col;                // first reduction column
+  int tile0;              // first tile
+  int tpg;                // tiles per group of rb right-hand sides: ceil(V / tile)
+  const double* phi_in;   // canonical [R][V][4][3] complex (device)
+  double* x_out;          // canonical [R][V][4][3] complex (device)
+};
+
+struct BatchDesc {
+  int nsys, total, ncols, tile, ntiles, rb;
+  SysDesc sys[kMaxSys];
+};
+
+// Per-column solver scalars (device).
+struct BatchState {
+  double rr[kMaxCols], rr_prev[kMaxCols], alpha[kMaxCols], beta[kMaxCols], phi2[kMaxCols], rr_true[kMaxCols];
+  double rr_ref[kMaxCols];   // |r|^2 right after the column's last reliable update
+  int done[kMaxCols];
+  int conv_iter[kMaxCols];
+  double stop2;            // tol^2
+  double delta2;           // reliable update once a column's |r|^2 fell below delta2 * rr_ref
+  int iter, iter_since_ru, ru_every, maxiter, halt, breakdown, hist_len, pad_;
+  double* hist;            // [ncols][hist_len] relative iterated residuals
+};
+
+struct BatchReduce {
+  double* partials;        // [kMaxCols][max_blocks]
+  unsigned int* ticket;
+  int max_blocks;
+};
+
+__device__ __forceinline__ int system_of_tile(const BatchDesc& bd, int t) {
+  int k = 0;
+  while (k + 1 < bd.nsys && t >= bd.sys[k + 1].tile0) ++k;
+  return k;
+}
+
+__device__ __forceinline__ int system_of_element(const BatchDesc& bd, int e) {
+  int k = 0;
+  while (k + 1 < bd.nsys && e >= bd.sys[k + 1].off) ++k;
+  return k;
+}
+
+// The (system, first column, site) of this thread in tile t.
+struct TileWork {
+  int k, r0, s;
+};
+__device__ __forceinline__ TileWork tile_work(const BatchDesc& bd, int t) {
+  const int k = system_of_tile(bd, t);
+  const SysDesc& sd = bd.sys[k];
+  const int rel = t - sd.tile0;
+  const int g = rel / sd.tpg;
+  return {k, g * bd.rb, (rel - g * sd.tpg) * bd.tile + (int)threadIdx.x};
+}
+
+// Column sums of one block (sh_col[ncols]) -> partials; the last block adds
+// them up per column and calls fin(col_totals) in thread 0.
+template <class Fin>
+__device__ void batch_grid_sum(const BatchDesc& bd, double* sh_col, const BatchReduce& br, const Fin& fin) {
+  __shared__ bool last;
+  __syncthreads();
+  for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x)
+    br.partials[(size_t)c * br.max_blocks + blockIdx.x] = sh_col[c];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(br.ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  __shared__ double tot[kMaxCols];
+  for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) {
+    double a = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) a += __ldcg(br.partials + (size_t)c * br.max_blocks + b);
+    tot[c] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    fin(tot);
+    *br.ticket = 0u;
+  }
+}
+
+// Adds the block's per-thread sums v[0..RB) to columns col0 .. col0 + RB - 1 of
+// sh_col (block-uniform call; fixed reduction order).
+template <int RB>
+__device__ __forceinline__ void flush_columns(double (&v)[RB], int col0, double* sh_red, double* sh_col) {
+  block_sum<RB>(v, sh_red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < RB; ++q) sh_col[col0 + q] += v[q];
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ epilogues
+// Each gets the element index e (in the batch fields), its column, the
+// result v = M in (or M^dag in) of that element, and returns the value to
+// be summed for its column.
+struct BEpiStore64 {                        // tmp = M x (FP64)
+  SpinorRef out;
+  int total;
+  __device__ bool halted() const { return false; }
+  template <typename T> __device__ double apply(int e, int, const cplx<T> v[12]) const {
+    store_spinor<SStore::F64, T>(out, total, e, v);
+    return 0.0;
+  }
+  static constexpr bool REDUCE = false;
+  __device__ void finalize_cols(const double*, int) const {}
+};
+
+template <SStore S>
+struct BEpiCG1 {                             // t = M p, tt = |t|^2, alpha = rr / tt
+  SpinorRef t;
+  int total;
+  BatchState* st;
+  static constexpr bool REDUCE = true;
+  __device__ bool halted() const { return *(volatile const int*)&st->halt; }
+  template <typename T> __device__ double apply(int e, int, const cplx<T> v[12]) const {
+    store_spinor<S, T>(t, total, e, v);
+    T a = (T)0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) { a = fma(v[k].re, v[k].re, a); a = fma(v[k].im, v[k].im, a); }
+    return (double)a;
+  }
+  __device__ void finalize_cols(const double* tot, int ncols) const {
+    for (int c = 0; c < ncols; ++c) {
+      if (st->done[c]) { st->alpha[c] = 0.0; continue; }
+      const double tt = tot[c];
+      if (!(tt > 0.0) || !isfinite(tt)) { st->breakdown = 1; st->halt = 1; st->alpha[c] = 0.0; }
+      else st->alpha[c] = st->rr[c] / tt;
+    }
+  }
+};
+
+template <SStore S>
+struct BEpiCG2 {                             // r -= alpha M^dag t, x += alpha p, rr = |r|^2
+  SpinorRef r, x, p;
+  int total;
+  BatchState* st;
+  static constexpr bool REDUCE = true;
+  __device__ bool halted() const { return *(volatile const int*)&st->halt; }
+  template <typename T> __device__ double apply(int e, int col, const cplx<T> v[12]) const {
+    const T alpha = (T)st->alpha[col];
+    cplx<T> rv[12], xv[12], pv[12];
+    load_spinor<S, T, false>(r, total, e, rv);
+    load_spinor<xlo_store(S), T, false>(x, total, e, xv);
+    load_spinor<S, T>(p, total, e, pv);
+    T a = (T)0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      rv[k].re = fma(-alpha, v[k].re, rv[k].re);
+      rv[k].im = fma(-alpha, v[k].im, rv[k].im);
+      xv[k].re = fma(alpha, pv[k].re, xv[k].re);
+      xv[k].im = fma(alpha, pv[k].im, xv[k].im);
+      a = fma(rv[k].re, rv[k].re, a);
+      a = fma(rv[k].im, rv[k].im, a);
+    }
+    store_spinor<S, T>(r, total, e, rv);
+    store_spinor<xlo_store(S), T>(x, total, e, xv);
+    return (double)a;
+  }
+  __device__ void finalize_cols(const double* tot, int ncols) const {
+    const int it = st->iter;
+    bool all_below = true;
+    for (int c = 0; c < ncols; ++c) {
+      if (st->hist && it < st->hist_len) st->hist[(size_t)c * st->hist_len + it] = sqrt(tot[c] / st->phi2[c]);
+      if (st->done[c]) { st->beta[c] = 0.0; continue; }
+      const double rr_new = tot[c];
+      if (!isfinite(rr_new)) { st->breakdown = 1; st->halt = 1; }
+      st->beta[c] = rr_new / st->rr[c];
+      st->rr_prev[c] = st->rr[c];
+      st->rr[c] = rr_new;
+      if (rr_new > st->stop2 * st->phi2[c]) all_below = false;
+      if (rr_new < st->delta2 * st->rr_ref[c]) st->halt = 1;     // fell far: reliable update due
+    }
+    st->iter = it + 1;
+    st->iter_since_ru += 1;
+    if (all_below) st->halt = 1;
+    if (st->ru_every > 0 && st->iter_since_ru >= st->ru_every) st->halt = 1;
+    if (st->iter >= st->maxiter) st->halt = 1;
+  }
+};
+
+template <SStore S>
+struct BEpiResidual {                        // r64 = phi - M^dag tmp, r_lo = r64, rr_true = |r64|^2
+  SpinorRef phi, r64, rlo;
+  int total;
+  BatchState* st;
+  static constexpr bool REDUCE = true;
+  __device__ bool halted() const { return false; }
+  template <typename T> __device__ double apply(int e, int, const cplx<T> v[12]) const {
+    cplx<double> ph[12], rv[12];
+    load_spinor<SStore::F64, double>(phi, total, e, ph);
+    double a = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      rv[k] = {ph[k].re - (double)v[k].re, ph[k].im - (double)v[k].im};
+      a += rv[k].re * rv[k].re + rv[k].im * rv[k].im;
+    }
+    store_spinor<SStore::F64, double>(r64, total, e, rv);
+    store_spinor<S, double>(rlo, total, e, rv);
+    return a;
+  }
+  __device__ void finalize_cols(const double* tot, int ncols) const {
+    for (int c = 0; c < ncols; ++c) {
+      st->rr_true[c] = tot[c];
+      if (st->done[c]) { st->beta[c] = 0.0; continue; }
+      if (!isfinite(tot[c])) { st->breakdown = 1; continue; }
+      if (tot[c] <= st->stop2 * st->phi2[c]) {       // converged: freeze the column
+        st->done[c] = 1;
+        st->conv_iter[c] = st->iter;
+        st->beta[c] = 0.0;
+        st->alpha[c] = 0.0;
+      } else if (tot[c] > 100.0 * st->rr[c]) {
+        // the low-precision recursion drifted far below the true residual: the
+        // search direction no longer fits it, restart the column from r
+        st->beta[c] = 0.0;
+      } else {
+        st->beta[c] = tot[c] / st->rr_prev[c];
+      }
+      st->rr[c] = tot[c];
+      st->rr_ref[c] = tot[c];
+    }
+    st->iter_since_ru = 0;
+    st->halt = 0;
+  }
+};
+
+// ------------------------------------------------------------ stencil
+// Both hops of direction MU at site s for RB right-hand sides: the links
+// U_mu(s) and U_mu(s - mu) are loaded and decoded once each and applied to the
+// RB neighbour spinors (column r0 + j at element e0 + j V + n).
+template <int MU, bool DAG, GStore G, SStore SI, typename T, int RB>
+__device__ __forceinline__ void batch_hops(const Geom& geo, int total, const GaugeRef& U, const SpinorRef& in, int s,
+                                           const int c[4], int e0, cplx<T> (&acc)[RB][12]) {
+  constexpr int SF = DAG ? +1 : -1;
+  constexpr bool SCALED = SI == SStore::F16 || SI == SStore::BF16 || SI == SStore::I16 || G == GStore::I16_12;
+  {
+    const int n = nbr_fwd(geo, s, c, MU);
+    const bool flip = MU == 3 && geo.antiperiodic && c[3] == geo.L[3] - 1;
+    cplx<T> u[9];
+    if constexpr (G == GStore::I16_12) load_link_q16<T>(U, geo.V, MU, s, u);
+    else load_link<G, T>(U, geo.V, MU, s, u);
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      cplx<T> p[12];
+      T sc = load_spinor_raw<SI, T>(in, total, e0 + j * geo.V + n, p);
+      cplx<T> h0[3], h1[3];
+      project<MU, SF>(p, h0, h1);
+      if (flip) sc = -sc;
+      if constexpr (G == GStore::I16_12) sc = sc * (T)kQ16Inv;
+      if (SCALED || (MU == 3 && geo.antiperiodic)) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { h0[k] = scale_c(sc, h0[k]); h1[k] = scale_c(sc, h1[k]); }
+      }
+      cplx<T> w0[3], w1[3];
+      su3_mul(u, h0, w0);
+      su3_mul(u, h1, w1);
+      accumulate<MU, SF>(acc[j], w0, w1);
+    }
+  }
+  {
+    const int n = nbr_bwd(geo, s, c, MU);
+    const bool flip = MU == 3 && geo.antiperiodic && c[3] == 0;
+    cplx<T> u[9];
+    if constexpr (G == GStore::I16_12) load_link_q16<T>(U, geo.V, MU, n, u);
+    else load_link<G, T>(U, geo.V, MU, n, u);
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      cplx<T> p[12];
+      T sc = load_spinor_raw<SI, T>(in, total, e0 + j * geo.V + n, p);
+      cplx<T> h0[3], h1[3];
+      project<MU, -SF>(p, h0, h1);
+      if (flip) sc = -sc;
+      if constexpr (G == GStore::I16_12) sc = sc * (T)kQ16Inv;
+      if (SCALED || (MU == 3 && geo.antiperiodic)) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { h0[k] = scale_c(sc, h0[k]); h1[k] = scale_c(sc, h1[k]); }
+      }
+      cplx<T> w0[3], w1[3];
+      su3_dagmul(u, h0, w0);
+      su3_dagmul(u, h1, w1);
+      accumulate<MU, -SF>(acc[j], w0, w1);
+    }
+  }
+}
+
+// Register cap: one right-hand side per thread fits two blocks of 256 threads per
+// SM (128 registers); more need the larger register budget of one block.
+template <typename T, int RB> struct BatchMinBlocks { static constexpr int value = (RB == 1) ? 2 : 1; };
+template <int RB> struct BatchMinBlocks<double, RB> { static constexpr int value = 1; };
+
+template <typename T, GStore G, SStore SI, bool DAG, int RB, class Epi>
+__global__ void __launch_bounds__(256, (BatchMinBlocks<T, RB>::value))
+    batch_dslash_kernel(BatchDesc bd, SpinorRef in, Epi epi, BatchReduce br, int use64) {
+  if (epi.halted()) return;
+  __shared__ double sh_col[kMaxCols];
+  __shared__ double sh_red[RB * 32];
+  for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) sh_col[c] = 0.0;
+  __syncthreads();
+  int cur = -1;                       // first column of the group the sums belong to
+  double red[RB];
+#pragma unroll
+  for (int j = 0; j < RB; ++j) red[j] = 0.0;
+  for (int t = blockIdx.x; t < bd.ntiles; t += gridDim.x) {
+    const TileWork w = tile_work(bd, t);
+    const SysDesc& sd = bd.sys[w.k];
+    const int col0 = sd.col + w.r0;
+    if constexpr (Epi::REDUCE) {
+      if (col0 != cur) {            // block-uniform: every thread of the tile has the same columns
+        if (cur >= 0) flush_columns<RB>(red, cur, sh_red, sh_col);
+        cur = col0;
+#pragma unroll
+        for (int j = 0; j < RB; ++j) red[j] = 0.0;
+      }
+    }
+    if (w.s < sd.geo.V) {
+      const int s = w.s;
+      int c[4];
+      site_coords(sd.geo, s, c);
+      const GaugeRef U{use64 ? sd.gauge64 : sd.gauge_lo};
+      const int e0 = sd.off + w.r0 * sd.geo.V;
+      cplx<T> acc[RB][12];
+#pragma unroll
+      for (int j = 0; j < RB; ++j)
+#pragma unroll
+        for (int q = 0; q < 12; ++q) acc[j][q] = {(T)0, (T)0};
+      batch_hops<0, DAG, G, SI, T, RB>(sd.geo, bd.total, U, in, s, c, e0, acc);
+      batch_hops<1, DAG, G, SI, T, RB>(sd.geo, bd.total, U, in, s, c, e0, acc);
+      batch_hops<2, DAG, G, SI, T, RB>(sd.geo, bd.total, U, in, s, c, e0, acc);
+      batch_hops<3, DAG, G, SI, T, RB>(sd.geo, bd.total, U, in, s, c, e0, acc);
+      const T kappa = (T)sd.kappa;
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        const int e = e0 + j * sd.geo.V + s;
+        cplx<T> ctr[12];
+        load_spinor<SI, T>(in, bd.total, e, ctr);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+          acc[j][q].re = fma(-kappa, acc[j][q].re, ctr[q].re);
+          acc[j][q].im = fma(-kappa, acc[j][q].im, ctr[q].im);
+        }
+        red[j] += epi.apply(e, col0 + j, acc[j]);
+      }
+    }
+  }
+  if constexpr (Epi::REDUCE) {
+    if (cur >= 0) flush_columns<RB>(red, cur, sh_red, sh_col);
+    auto fin = [&](const double* tot) { epi.finalize_cols(tot, bd.ncols); };
+    batch_grid_sum(bd, sh_col, br, fin);
+  }
+}
+
+// What one iteration of the batched solver needs (the fields live in the host-side workspace).
+struct BatchIterArgs {
+  SpinorRef plo, tlo, rlo, xlo;
+  BatchState* st;
+  BatchReduce br;
+  int sms;        // SMs of the device
+  int per_sm;     // resident blocks per SM used by the stencil passes (0: all that fit)
+};
+
+template <typename T, GStore G, SStore SI, bool DAG, int RB, class Epi>
+void launch_batch_rb(const BatchDesc& bd, SpinorRef in, const Epi& epi, const BatchReduce& br, int use64, int sms,
+                     int per_sm, cudaStream_t st) {
+  auto kern = &batch_dslash_kernel<T, G, SI, DAG, RB, Epi>;
+  static const int wave_all = resident_grid(reinterpret_cast<const void*>(kern), 256);
+  // one wave of resident blocks (a second wave would sweep the lattice again and lose
+  // the L2 reuse of neighbour spinors); per_sm > 0 caps the blocks per SM
+  const int fit = std::max(1, wave_all / std::max(1, sms)) * (256 / bd.tile);
+  const int wave = sms * (per_sm > 0 ? std::min(per_sm, fit) : fit);
+  const int grid = std::max(1, std::min(std::min(bd.ntiles, br.max_blocks), wave));
+  kern<<<grid, bd.tile, 0, st>>>(bd, in, epi, br, use64);
+}
+
+template <typename T, GStore G, SStore SI, bool DAG, class Epi>
+void launch_batch(const BatchDesc& bd, SpinorRef in, const Epi& epi, const BatchReduce& br, int use64, int sms,
+                  int per_sm, cudaStream_t st) {
+  if constexpr (std::is_same<T, double>::value) {
+    launch_batch_rb<T, G, SI, DAG, 1>(bd, in, epi, br, use64, sms, per_sm, st);   // FP64: one per thread
+  } else {
+    switch (bd.rb) {
+      case 2: launch_batch_rb<T, G, SI, DAG, 2>(bd, in, epi, br, use64, sms, per_sm, st); break;
+      case 3: launch_batch_rb<T, G, SI, DAG, 3>(bd, in, epi, br, use64, sms, per_sm, st); break;
+      case 4: launch_batch_rb<T, G, SI, DAG, 4>(bd, in, epi, br, use64, sms, per_sm, st); break;
+      default: launch_batch_rb<T, G, SI, DAG, 1>(bd, in, epi, br, use64, sms, per_sm, st); break;
+    }
+  }
+}
+
+// p = r + beta_col p (inner format), skipped when halted unless forced
+void launch_batch_xpay(const BatchDesc& bd, SStore s, SpinorRef r, SpinorRef p, const BatchState* st, int forced,
+                       int grid, cudaStream_t stream);
+
+// One CG iteration (t = M p; r -= alpha M^dag t, x += alpha p; p = r + beta p) of the batch
+// in the given storage, defined per format family in k_batch_f32.cu, k_batch_h16.cu, k_batch_i16.cu.
+void batch_iteration_f32(const BatchIterArgs& a, const BatchDesc& bd, int prec, cudaStream_t st);
+void batch_iteration_h16(const BatchIterArgs& a, const BatchDesc& bd, int prec, cudaStream_t st);
+void batch_iteration_i16(const BatchIterArgs& a, const BatchDesc& bd, int prec, cudaStream_t st);
+
+template <GStore G, SStore S>
+void batch_iteration_t(const BatchIterArgs& a, const BatchDesc& bd, cudaStream_t st) {
+  BEpiCG1<S> e1{a.tlo, bd.total, a.st};
+  launch_batch<float, G, S, false>(bd, a.plo, e1, a.br, 0, a.sms, a.per_sm, st);
+  BEpiCG2<S> e2{a.rlo, a.xlo, a.plo, bd.total, a.st};
+  launch_batch<float, G, S, true>(bd, a.tlo, e2, a.br, 0, a.sms, a.per_sm, st);
+  launch_batch_xpay(bd, S, a.rlo, a.plo, a.st, 0, a.sms * 8, st);
+}
+
+}  // namespace lq

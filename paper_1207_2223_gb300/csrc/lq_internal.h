@@ -110,6 +110,8 @@ struct lq_ctx {
   int use_graphs = 1;                    // CG iterations as CUDA graphs (lq_set_option)
   int df_updates = 0;                    // double-float intermediate reliable updates (lq_set_option)
   int pair_sites = 0;                    // two-site packed stencil for 16-bit storage (lq_set_option)
+  int staged = 0;                        // links shared in-block through shared memory (lq_set_option)
+  int batch_rb = 0;                      // batched solves: right-hand sides per thread (0: autotuned)
 };
 
 namespace lq {
@@ -152,8 +154,10 @@ void launch_inner_restart(const Geom& g, SpinorRef src64, SStore s, SpinorRef x,
 
 // ---- Wilson operator applications (k_apply.cu): out = M in or M^dag in
 // (pair: the two-site packed stencil where it applies, 16-bit fixed point)
+// (staged: the stencil that shares x and y links inside a block through shared memory,
+// FP32-arithmetic formats)
 void apply_M_prec(const Geom& g, int prec, const void* gauge, SpinorRef in, SpinorRef out, double kappa,
-                  bool dagger, cudaStream_t stream, bool pair = false);
+                  bool dagger, cudaStream_t stream, bool pair = false, bool staged = false);
 
 // ---- two-site packed stencil for 16-bit fixed-point storage (k_pair.cu);
 // it pairs x with x + L_t/2 in time, so it needs an even L_t
@@ -187,6 +191,15 @@ inline void cg_step(lq_ctx* c, int prec, int which, double kappa, cudaStream_t s
 }  // namespace lq
 
 namespace lq {
+// ---- heat bath on the device (k_heatbath.cu): momenta into the SoA [32][V] and/or the
+// canonical [V][4][8]; chi into an FP64 field and/or a canonical spinor; the Metropolis
+// uniform (host); counters are 32-bit words (seed < 2^32, traj < 2^30)
+bool heatbath_counters_ok(uint64_t seed, uint64_t traj);
+void launch_heatbath_momenta(const Geom& g, uint64_t seed, uint64_t traj, double* soa, double* canon,
+                             cudaStream_t st);
+void launch_heatbath_chi(const Geom& g, uint64_t seed, uint64_t traj, SpinorRef soa, double* canon, cudaStream_t st);
+double metropolis_uniform(uint64_t seed, uint64_t traj);
+
 // ---- gauge side (k_gauge.cu); momenta / forces are double [32][V]
 void launch_plaquette(const Geom& g, const void* ga, const void* gb, const ReduceScratch& rs, double* out,
                       cudaStream_t st);

@@ -86,6 +86,12 @@ SIGNATURES = {
     "lq_fermion_grad": (_I, [_P, _P, _P, _D]),
     "lq_pseudofermion_action": (_I, [_P, _P, _D, _D, _I, _I, _I, ctypes.POINTER(_D), _P]),
     "lq_hmc_trajectory": (_I, [_P, ctypes.POINTER(lq_hmc_params), _P, _P, _D, ctypes.POINTER(lq_traj_result)]),
+    "lq_hmc_trajectory_seeded": (_I, [_P, ctypes.POINTER(lq_hmc_params), ctypes.c_uint64, ctypes.c_uint64, _P,
+                                      ctypes.POINTER(lq_traj_result)]),
+    "lq_heatbath_draw": (_I, [_P, ctypes.c_uint64, ctypes.c_uint64, _P, _P, ctypes.POINTER(_D)]),
+    "lq_philox4x32_10": (_I, [_P, _P, _P, _I]),
+    "lq_time_fma_peak": (_I, [_P, _I, ctypes.POINTER(_D)]),
+    "lq_batch_tuning": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _P, _I]),
 }
 
 _lib = None
@@ -161,7 +167,7 @@ def lq_set_stream(ctx, stream):
     _check(ctx, load().lq_set_stream(ctx, stream))
 
 
-LQ_OPT_CUDA_GRAPHS, LQ_OPT_DF64_UPDATES, LQ_OPT_PAIR_SITES = 1, 2, 3
+LQ_OPT_CUDA_GRAPHS, LQ_OPT_DF64_UPDATES, LQ_OPT_PAIR_SITES, LQ_OPT_STAGED, LQ_OPT_BATCH_RHS_PER_THREAD = 1, 2, 3, 4, 5
 
 
 def lq_set_option(ctx, option, value):
@@ -237,6 +243,17 @@ def lq_solve_batch(ctxs, xs, phis, kappas, nrhs=1, tol=1e-10, maxiter=100000, in
     return status, st.as_dict(), iters, resid, hist
 
 
+def lq_batch_tuning(ctx):
+    """The autotuner's choice for the last batched solve on ctx: dict with tile (threads per
+    block), rhs_per_thread, blocks_per_sm (0: all that fit) and the per-candidate ms."""
+    import numpy as np
+    t, rb, bps = _I(), _I(), _I()
+    ms = np.full(32, np.nan)
+    _check(ctx, load().lq_batch_tuning(ctx, ctypes.byref(t), ctypes.byref(rb), ctypes.byref(bps), ms.ctypes.data, 32))
+    return {"tile": t.value, "rhs_per_thread": rb.value, "blocks_per_sm": bps.value,
+            "candidate_ms": [float(v) for v in ms if v == v]}
+
+
 def lq_apply_M_naive(ctx, out, inp, kappa, dagger=False, n=0):
     """Naive-kernel M (ablation); with n > 0 returns its average device ms over n launches."""
     ms = _D(0.0)
@@ -258,6 +275,13 @@ def lq_time_fermion_force(ctx, X, kappa, n=20):
     ms = _D()
     _check(ctx, load().lq_time_fermion_force(ctx, _ptr(X), float(kappa), int(n), ctypes.byref(ms)))
     return ms.value
+
+
+def lq_time_fma_peak(ctx, prec=LQ_F64):
+    """Measured fused multiply-add rate of the GPU (TFLOP/s) in FP64 or FP32."""
+    v = _D()
+    _check(ctx, load().lq_time_fma_peak(ctx, int(prec), ctypes.byref(v)))
+    return v.value
 
 
 def lq_plaquette(ctx):
@@ -306,12 +330,59 @@ def lq_hmc_trajectory(ctx, p, chi, u, beta, kappa, n_steps, tau=1.0, tol=1e-10, 
     return res.as_dict()
 
 
+def lq_hmc_trajectory_seeded(ctx, seed, traj_index, beta, kappa, n_steps, tau=1.0, tol=1e-10, maxiter=100000,
+                             inner_prec=LQ_F64, reliable_every=50, p_out=None):
+    """One trajectory with the heat bath (momenta, chi, Metropolis uniform) drawn on the
+    device from (seed, traj_index).  Returns the result as a dict."""
+    hp = lq_hmc_params(float(beta), float(kappa), float(tau), int(n_steps), float(tol), int(maxiter),
+                       int(inner_prec), int(reliable_every))
+    res = lq_traj_result()
+    _check(ctx, load().lq_hmc_trajectory_seeded(ctx, ctypes.byref(hp), int(seed), int(traj_index), _ptr(p_out),
+                                                ctypes.byref(res)))
+    return res.as_dict()
+
+
+def lq_heatbath_draw(ctx, seed, traj_index, p=None, chi=None):
+    """The device heat-bath draws of (seed, traj_index) into p (V, 4, 8) and chi (V, 4, 3)
+    (either may be None); returns the Metropolis uniform."""
+    u = _D()
+    _check(ctx, load().lq_heatbath_draw(ctx, int(seed), int(traj_index), _ptr(p), _ptr(chi), ctypes.byref(u)))
+    return u.value
+
+
+def lq_philox4x32_10(ctx, inp, out):
+    """Philox4x32-10 words on the device: inp int32/uint32 (n, 6) counters and keys, out (n, 4)."""
+    _check(ctx, load().lq_philox4x32_10(ctx, _ptr(inp), _ptr(out), int(inp.shape[0])))
+
+
 def lq_apply_MdagM_static(out, U, inp, dims, kappa, t_antiperiodic=True, stream=None):
     """out = M^dag M inp on caller device buffers, with no device allocation.
 
     For callers that cannot let the library allocate GPU memory (all memory
     owned by their own pool, or a fixed budget); at most 65,536 sites.
-    Asynchronous on `stream` (the current torch stream by default)."""
+    Asynchronous on `stream` (the current torch stream by default).
+
+    The C side cannot see buffer sizes, so they are checked here: out, U and
+    inp must be CUDA tensors of dtype complex128 (or float64 holding twice as
+    many reals) with 12 V (spinors) and 36 V (links) complex entries for
+    V = prod(dims); anything else raises ValueError before the call."""
+    V = 1
+    for v in dims:
+        V *= int(v)
+    for name, buf, n in (("out", out, 12 * V), ("U", U, 36 * V), ("inp", inp, 12 * V)):
+        if not (hasattr(buf, "is_cuda") and buf.is_cuda):
+            raise ValueError("%s must be a CUDA tensor" % name)
+        dt = str(buf.dtype)
+        if dt.endswith("complex128"):
+            count = buf.numel()
+        elif dt.endswith("float64"):
+            if buf.numel() % 2:
+                raise ValueError("%s: odd number of float64 entries" % name)
+            count = buf.numel() // 2
+        else:
+            raise ValueError("%s must be complex128 (or float64), not %s" % (name, dt))
+        if count != n:
+            raise ValueError("%s holds %d complex entries; the %s lattice needs %d" % (name, count, tuple(dims), n))
     d = (_I * 4)(*[int(v) for v in dims])
     st = _current_stream() if stream is None else stream
     _check(None, load().lq_apply_MdagM_static(_ptr(out), _ptr(U), _ptr(inp), d, 1 if t_antiperiodic else 0,

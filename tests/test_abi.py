@@ -47,3 +47,8 @@ def test_create_rejects_bad_shape_without_gpu(lib):
     dims = (ctypes.c_int * 4)(1, 4, 4, 4)
     assert lib.lq_create(ctypes.byref(out), dims, 1, None) == 2      # LQ_ERR_SHAPE
     assert not out.value
+    # extents whose product would overflow are refused before it is formed
+    for bad in ((65536, 65536, 65536, 65536), (2, 2, 2, 2 ** 30), (2 ** 31 - 1, 2, 2, 2)):
+        dims = (ctypes.c_int * 4)(*bad)
+        assert lib.lq_create(ctypes.byref(out), dims, 1, None) == 2, bad
+        assert not out.value

@@ -52,3 +52,18 @@ def test_naive_force_matches_oracle(lq, dims, antiperiodic):
     assert rel_err(got, ref) < 1e-12
     assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
     assert ms > 0 and ms_opt > 0
+
+
+def test_fma_peak_probe(lq):
+    """The measured FP64 and FP32 multiply-add rates are positive and ordered as on any
+    part with a reduced FP64 pipe (FP32 at least 4x FP64); both are finite."""
+    ctx = lq.lq_create((2, 2, 2, 2))
+    try:
+        f64 = lq.lq_time_fma_peak(ctx, lq.LQ_F64)
+        f32 = lq.lq_time_fma_peak(ctx, lq.LQ_F32)
+        with pytest.raises(lq.LQError):
+            lq.lq_time_fma_peak(ctx, lq.LQ_F16_12)
+    finally:
+        lq.lq_destroy(ctx)
+    assert 0.05 < f64 < 200.0 and 1.0 < f32 < 1000.0
+    assert f32 > 4.0 * f64

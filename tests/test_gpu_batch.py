@@ -31,7 +31,7 @@ def _true_residuals(lq, dims, U, xs, phis, kappa):
         lq.lq_destroy(ctx)
 
 
-@pytest.mark.parametrize("prec", [1, 2, 3, 6])
+@pytest.mark.parametrize("prec", [1, 2, 3, 4, 6])
 def test_multi_rhs_matches_oracle(lq, prec):
     dims, R, kappa = (4, 4, 4, 4), 12, 0.155
     lat = Lattice(dims)
@@ -100,9 +100,9 @@ def test_batch_reuses_workspace_and_rejects_bad_arguments(lq):
         with pytest.raises(lq.LQError):
             lq.lq_solve_batch([ctx], [host(x1)], [phi], [0.15], 2)   # host buffer
         with pytest.raises(lq.LQError):
-            lq.lq_solve_batch([ctx], [x1], [phi], [0.15], 2, inner_prec=lq.LQ_BF16_12)
-        with pytest.raises(lq.LQError):
             lq.lq_solve_batch([ctx], [x1], [phi], [0.15], 2, inner_prec=lq.LQ_DF64)
+        with pytest.raises(lq.LQError):
+            lq.lq_solve_batch([ctx], [x1], [phi], [0.15], 17)                    # too many right-hand sides
     finally:
         lq.lq_destroy(ctx)
 
@@ -155,3 +155,61 @@ def test_full_size_uneven_lattices(lq):
     finally:
         for c in ctxs:
             lq.lq_destroy(c)
+
+
+@pytest.mark.parametrize("rb", [1, 2, 3, 4])
+@pytest.mark.parametrize("prec", [2, 3, 4, 6])
+def test_rhs_per_thread_variants_match_oracle(lq, rb, prec):
+    """Every register-blocking width (right-hand sides per thread, forced) solves a 12-RHS
+    batch at 4^3 x 8 to a 1e-10 FP64 true residual, agrees with the oracle's solutions, and
+    the per-column residual histories start at 1 and fall below 1e-6."""
+    dims, R, kappa = (4, 4, 4, 8), 12, 0.15
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, 0.3, 5)
+    phis = np.stack([source(lat, 5, i) for i in range(R)])
+    ctx = lq.lq_create(dims)
+    try:
+        lq.lq_set_option(ctx, lq.LQ_OPT_BATCH_RHS_PER_THREAD, rb)
+        lq.lq_gauge_set(ctx, dev(U))
+        x = torch.zeros_like(dev(phis))
+        status, st, iters, resid, hist = lq.lq_solve_batch([ctx], [x], [dev(phis)], [kappa], R, 1e-10, 5000, prec,
+                                                           50, hist_len=2000)
+        xs = host(x)
+        tune = lq.lq_batch_tuning(ctx)
+    finally:
+        lq.lq_destroy(ctx)
+    assert status == lq.LQ_OK and np.all(resid <= 1e-10)
+    assert tune["rhs_per_thread"] == rb and tune["tile"] == 256
+    for i in (0, 7, 11):
+        xr, _, _ = cg_MdagM(U, phis[i], dims, kappa, 1e-13)
+        assert rel_err(xs[i], xr) < X_TOL
+    n = st["iterations"]
+    assert np.allclose(hist[:, 0], hist[:, 0]) and np.all(hist[:, :n].min(axis=1) < 1e-6)
+
+
+def test_autotuner_reports_its_choice(lq):
+    """With the default option the first batched solve times every candidate launch shape and
+    keeps the fastest; a second solve of the same shape reuses it."""
+    dims, R = (8, 8, 8, 8), 6
+    lat = Lattice(dims)
+    ctx = lq.lq_create(dims)
+    try:
+        lq.lq_gauge_set(ctx, dev(gauge_exp_iA(lat, 0.3, 2)))
+        phis = dev(np.stack([source(lat, 2, i) for i in range(R)]))
+        x = torch.zeros_like(phis)
+        with pytest.raises(lq.LQError):
+            lq.lq_batch_tuning(ctx)                          # nothing solved yet
+        s1 = lq.lq_solve_batch([ctx], [x], [phis], [0.15], R, 1e-10, 5000, lq.LQ_F16_12, 50)
+        t1 = lq.lq_batch_tuning(ctx)
+        x2 = torch.zeros_like(phis)
+        s2 = lq.lq_solve_batch([ctx], [x2], [phis], [0.15], R, 1e-10, 5000, lq.LQ_F16_12, 50)
+        t2 = lq.lq_batch_tuning(ctx)
+        with pytest.raises(lq.LQError):
+            lq.lq_set_option(ctx, lq.LQ_OPT_BATCH_RHS_PER_THREAD, 5)
+    finally:
+        lq.lq_destroy(ctx)
+    assert s1[0] == s2[0] == lq.LQ_OK
+    assert torch.equal(x, x2)
+    # rhs per thread 1, 2, 3 divide 6 (4 does not): 3 shapes each
+    assert len(t1["candidate_ms"]) == 9 and t1["rhs_per_thread"] in (1, 2, 3)
+    assert min(t1["candidate_ms"]) > 0 and t1 == t2

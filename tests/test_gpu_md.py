@@ -144,9 +144,11 @@ def test_trajectory_small_preset_fp64(lq):
     assert np.max(np.abs(Ug - ref["U"])) < 1e-10
 
 
-@pytest.mark.parametrize("prec", [1, 2, 3, 6])
+@pytest.mark.parametrize("prec", [1, 2, 3, 4, 6])
 def test_trajectory_mixed_precision_solves(lq, prec):
-    """Same trajectory with mixed-precision solves (FP64 true residual 1e-10 each)."""
+    """Same trajectory with mixed-precision solves (FP64 true residual 1e-10 each): Delta H
+    within 1e-8 of the FP64 oracle's, the same decision, and the final momenta and links
+    within the bounds of the FP64 trajectory."""
     dims = (4, 4, 4, 4)
     lat = Lattice(dims)
     U = gauge_exp_iA(lat, 0.3, 0)
@@ -156,11 +158,22 @@ def test_trajectory_mixed_precision_solves(lq, prec):
     ref = trajectory(U, p0, chi, u, dims, 5.6, 0.15, 10, 1.0, 1e-10)
     ctx = _ctx(lq, dims, U)
     try:
-        r = lq.lq_hmc_trajectory(ctx, dev(p0), dev(chi), u, 5.6, 0.15, 10, 1.0, 1e-10, 10000, prec, 50)
+        p = dev(p0)
+        r = lq.lq_hmc_trajectory(ctx, p, dev(chi), u, 5.6, 0.15, 10, 1.0, 1e-10, 10000, prec, 50)
+        Ug = np.empty_like(U)
+        lq.lq_gauge_get(ctx, Ug)
+        pg = host(p)
     finally:
         lq.lq_destroy(ctx)
-    assert abs(r["dH"] - ref["dH"]) < 1e-6, (r["dH"], ref["dH"])
+    # BF16 (8-bit significand): the solves still certify a 1e-10 FP64 residual, but the
+    # solution is no longer close to CG's Galerkin solution, so S_f = phi^dag X moves at
+    # first order in the residual r, |X^dag r| <= |X| |r| (measured 2.9e-8 here); the
+    # other formats stay within 1e-8 of the oracle
+    tol = 1e-7 if prec == 4 else 1e-8
+    assert abs(r["dH"] - ref["dH"]) < tol, (prec, r["dH"], ref["dH"])
     assert bool(r["accepted"]) == ref["accept"]
+    assert np.max(np.abs(pg - ref["p"])) < 1e-8
+    assert np.max(np.abs(Ug - ref["U"])) < 1e-10
 
 
 def test_trajectory_reject_restores_links(lq):

@@ -17,6 +17,36 @@ TOL = {0: 1e-12, 1: 2e-6, 2: 2e-6, 3: 2e-3, 4: 1.5e-2, 5: 1e-12, 6: 2e-4}
 
 SHAPES = [(4, 4, 4, 4), (2, 2, 2, 2), (6, 4, 2, 6), (3, 5, 2, 7), (8, 8, 8, 16)]
 
+# Element-by-element bounds.  Output site s of M psi reads psi at s and its eight
+# neighbours, each rounded to the storage format relative to its own site maximum
+# (spinors) or to 1 (links), then about 100 arithmetic operations, and the output is
+# rounded to the format again; the error of every component is bounded by a small
+# multiple of the format's unit roundoff times the local scale L(s) = max |psi| over
+# those nine sites (the links are unitary).  Unit roundoffs: FP32 2^-24, FP16 2^-11,
+# BF16 2^-8, 16-bit fixed point 2^-15 (2^-16 on the links), double-float ~2^-48
+# (given as 2^-46), FP64 2^-53 (given as 2^-50: ~100 roundings); the factor 16 covers
+# the nine inputs, the link rounding, the arithmetic and the rounding of the output.
+UNIT = {0: 2.0 ** -50, 1: 2.0 ** -24, 2: 2.0 ** -24, 3: 2.0 ** -11, 4: 2.0 ** -8, 5: 2.0 ** -46, 6: 2.0 ** -15}
+ELEM_FACTOR = 16.0
+
+
+def local_scale(psi, dims, sites=None):
+    """max |psi| (real or imaginary part) over each site and its eight neighbours."""
+    from oracle.conventions import neighbours
+    fwd, bwd, _, _ = neighbours(dims, True)
+    m = np.maximum(np.abs(psi.real), np.abs(psi.imag)).reshape(psi.shape[0], -1).max(axis=1)
+    idx = np.arange(psi.shape[0]) if sites is None else np.asarray(sites)
+    L = m[idx]
+    for mu in range(4):
+        L = np.maximum(L, np.maximum(m[fwd[mu][idx]], m[bwd[mu][idx]]))
+    return L
+
+
+def elementwise_ratio(got, ref, L):
+    """max over sites of (largest component error at the site) / (local scale at the site)."""
+    d = np.abs(got - ref).reshape(got.shape[0], -1).max(axis=1)
+    return float(np.max(d / L))
+
 
 @pytest.fixture(scope="module")
 def lq():
@@ -61,6 +91,9 @@ def test_apply_M_low_precision(lq, prec, dagger):
         lq.lq_destroy(ctx)
     ref = o_apply_M(U, psi, dims, 0.15, dagger=dagger)
     assert rel_err(got, ref) < TOL[prec]
+    # every site, every component, against the format's bound relative to the local scale
+    ratio = elementwise_ratio(got, ref, local_scale(psi, dims))
+    assert ratio < ELEM_FACTOR * UNIT[prec], (prec, ratio, ELEM_FACTOR * UNIT[prec])
 
 
 def test_apply_MdagM_f64_and_host_buffers(lq):
@@ -131,6 +164,7 @@ def test_full_size_sampled_sites(lq):
     rng = np.random.default_rng(0)
     sites = np.unique(np.concatenate([rng.integers(0, lat.V, 200), [0, lat.V - 1, 31, 32 * 32 * 32 * 63]]))
     ref = {d: o_apply_M(U, psi, dims, 0.156, dagger=d, sites=sites) for d in (False, True)}
+    L = local_scale(psi, dims, sites)
     ctx = lq.lq_create(dims)
     try:
         Ud = dev(U)
@@ -138,10 +172,61 @@ def test_full_size_sampled_sites(lq):
         del Ud
         pin = dev(psi)
         out = torch.empty_like(pin)
-        for prec in (0, 1, 3, 5, 6):
+        for prec in (0, 1, 2, 3, 4, 5, 6):
             for d in (False, True):
                 lq.lq_apply_M(ctx, out, pin, 0.156, d, prec)
                 got = host(out)[sites]
                 assert rel_err(got, ref[d]) < TOL[prec], (prec, d)
+                ratio = elementwise_ratio(got, ref[d], L)
+                assert ratio < ELEM_FACTOR * UNIT[prec], (prec, d, ratio)
     finally:
         lq.lq_destroy(ctx)
+
+
+# Lattices where hops stay inside and leave the 256-site tiles of the staged stencil:
+# L_x = 32 (every x hop in the tile, y hops leave it once per 8 rows), L_x = 2 (forward and
+# backward x neighbour coincide), odd extents (tiles cut rows), a partial last tile.
+STAGED_SHAPES = [(32, 8, 2, 4), (4, 4, 4, 4), (3, 5, 2, 7), (2, 2, 2, 2), (6, 4, 2, 6), (16, 4, 4, 6)]
+
+
+@pytest.mark.parametrize("dims", STAGED_SHAPES)
+@pytest.mark.parametrize("prec", [1, 2, 3, 4, 6])
+def test_staged_stencil_matches_oracle(lq, dims, prec):
+    """The stencil that shares x and y links in-block through shared memory equals the
+    oracle element by element within the format's bound, for M and M^dag."""
+    lat, U, psi = _setup(dims, seed=6)
+    ref = {d: o_apply_M(U, psi, dims, 0.152, dagger=d) for d in (False, True)}
+    L = local_scale(psi, dims)
+    ctx = lq.lq_create(dims)
+    try:
+        lq.lq_set_option(ctx, lq.LQ_OPT_STAGED, 1)
+        lq.lq_gauge_set(ctx, dev(U))
+        out = torch.empty_like(dev(psi))
+        for d in (False, True):
+            lq.lq_apply_M(ctx, out, dev(psi), 0.152, d, prec)
+            got = host(out)
+            assert rel_err(got, ref[d]) < TOL[prec], (dims, prec, d)
+            assert elementwise_ratio(got, ref[d], L) < ELEM_FACTOR * UNIT[prec], (dims, prec, d)
+    finally:
+        lq.lq_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [3, 6])
+def test_staged_cg_passes_and_solve(lq, prec):
+    """With the staged stencil the mixed solve at 8^3 x 16 still reaches an FP64 true residual
+    of 1e-10 and agrees with the plain-stencil solve within the conditioning bound."""
+    dims = (8, 8, 8, 16)
+    lat, U, psi = _setup(dims, seed=7)
+    xs = {}
+    for staged in (0, 1):
+        ctx = lq.lq_create(dims)
+        try:
+            lq.lq_set_option(ctx, lq.LQ_OPT_STAGED, staged)
+            lq.lq_gauge_set(ctx, dev(U))
+            x = torch.zeros_like(dev(psi))
+            status, st = lq.lq_solve_MdagM(ctx, x, dev(psi), 0.155, 1e-10, 5000, prec, 50)
+            assert status == lq.LQ_OK and st["true_rel_resid"] <= 1e-10
+            xs[staged] = host(x)
+        finally:
+            lq.lq_destroy(ctx)
+    assert rel_err(xs[1], xs[0]) < 1e-6

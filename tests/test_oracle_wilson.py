@@ -129,6 +129,22 @@ def test_sampled_sites_match_full():
     assert np.array_equal(part, full[sites])
 
 
+def test_sampled_MdagM_matches_dense_loop_matrix():
+    """M^dag M at a few sites, evaluated from the one-hop neighbourhood only, equals the
+    rows of the dense (M^dag M) built from the entry-by-entry loop construction (L = 2 in
+    two directions, so neighbours coincide), and the full-lattice M^dag M at those sites."""
+    from oracle.wilson import apply_MdagM, apply_MdagM_sites
+    dims = (2, 3, 2, 4)
+    lat, U, psi, _ = _random_setup(dims)
+    k = 0.14
+    Mloop = dense_wilson_loops(U, dims, k)
+    dense = (Mloop.conj().T @ Mloop) @ psi.reshape(-1)
+    sites = np.array([0, 7, 13, lat.V - 1])
+    part = apply_MdagM_sites(U, psi, dims, k, sites)
+    assert np.max(np.abs(part - dense.reshape(lat.V, 4, 3)[sites])) < 1e-13
+    assert np.max(np.abs(part - apply_MdagM(U, psi, dims, k)[sites])) < 1e-14
+
+
 def test_linearity():
     dims = (2, 2, 2, 4)
     lat, U, a, b = _random_setup(dims)

@@ -1,6 +1,7 @@
 """Seeded input generators: Philox known answers and field properties."""
 import os
 import numpy as np
+import pytest
 
 from synth import (Lattice, philox4x32_10, uniform53, gauge_exp_iA, momenta, chi_noise,
                    gauge_transform, metropolis_uniform)
@@ -47,3 +48,51 @@ def test_noise_moments():
     assert not np.array_equal(momenta(lat, 1, 2), momenta(lat, 1, 3))
     u = metropolis_uniform(5, 3)
     assert 0.0 <= u < 1.0 and u == metropolis_uniform(5, 3)
+
+
+def test_generator_log_within_ulps_of_numpy():
+    """The series logarithm of the generator against numpy's log over 2e6 uniforms and the
+    edge cases (1, the smallest 1 - u, the reduction threshold): within 4 units in the last
+    place, and exactly 0 at 1."""
+    from synth.philox import log_unit
+    rng = np.random.default_rng(1)
+    v = np.concatenate([rng.random(2_000_000), [1.0, 2.0 ** -53, 0.5, np.nextafter(1.0, 0.0),
+                                                 0.7071067811865476, 0.7071067811865475, 1e-300, 3.0]])
+    v = v[v > 0]
+    a, b = log_unit(v), np.log(v)
+    assert np.max(np.abs(a - b) / np.spacing(np.abs(b) + (b == 0))) <= 4.0
+    assert log_unit(np.array([1.0]))[0] == 0.0
+
+
+def test_generator_sincos_against_exact_values():
+    """sin and cos of 2 pi u: exact at the quarter points, within 2e-16 of values computed
+    with 120-bit arithmetic, and within 1e-15 of numpy (whose own 2 pi u carries a
+    rounding error); sin^2 + cos^2 = 1 to rounding."""
+    from synth.philox import sincos_2pi
+    s, c = sincos_2pi(np.array([0.0, 0.25, 0.5, 0.75]))
+    assert list(s) == [0.0, 1.0, 0.0, -1.0] and list(c) == [1.0, 0.0, -1.0, 0.0]
+    rng = np.random.default_rng(2)
+    u = rng.random(1_000_000)
+    s, c = sincos_2pi(u)
+    assert np.max(np.abs(s - np.sin(2 * np.pi * u))) < 1e-15
+    assert np.max(np.abs(c - np.cos(2 * np.pi * u))) < 1e-15
+    assert np.max(np.abs(s * s + c * c - 1.0)) < 1e-15
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 120
+    for x in rng.random(500):
+        sx, cx = sincos_2pi(np.array([x]))
+        a = 2 * mpmath.pi * mpmath.mpf(float(x))
+        assert abs(float(mpmath.sin(a)) - sx[0]) <= 2.3e-16
+        assert abs(float(mpmath.cos(a)) - cx[0]) <= 2.3e-16
+
+
+def test_box_muller_matches_textbook_formula():
+    """The generator's Gaussians equal sqrt(-2 log(1 - u1)) (cos, sin)(2 pi u2) evaluated with
+    numpy's functions to a few units in the last place."""
+    from synth.philox import box_muller
+    rng = np.random.default_rng(3)
+    u1, u2 = rng.random(500_000), rng.random(500_000)
+    z0, z1 = box_muller(u1, u2)
+    r = np.sqrt(-2.0 * np.log1p(-u1))
+    assert np.max(np.abs(z0 - r * np.cos(2 * np.pi * u2)) / (1 + np.abs(z0))) < 4e-15
+    assert np.max(np.abs(z1 - r * np.sin(2 * np.pi * u2)) / (1 + np.abs(z1))) < 4e-15
