@@ -61,7 +61,8 @@ typedef enum {
   LQ_ERR_CUDA = 3,           /* a CUDA runtime call failed */
   LQ_ERR_NOT_CONVERGED = 4,  /* iteration limit reached; the best iterate was still written */
   LQ_ERR_NAN = 5,            /* a non-finite value appeared (input or breakdown) */
-  LQ_ERR_STATE = 6           /* call out of order, e.g. no gauge field set yet */
+  LQ_ERR_STATE = 6,          /* call out of order, e.g. no gauge field set yet */
+  LQ_ERR_TIMEOUT = 7         /* a bounded device-side wait gave up (persistent batched iteration) */
 } lq_status;
 
 /* Storage / arithmetic precision of the operator and of the inner solver.
@@ -136,9 +137,18 @@ lq_status lq_set_stream(lq_ctx* ctx, void* cuda_stream);
  *   LQ_OPT_BATCH_RHS_PER_THREAD  0 (default): lq_solve_batch tunes its launch shape; 1..4:
  *                       every thread applies each link to this many right-hand sides (must
  *                       divide nrhs), 256 threads per block, no timing.  Changing it drops
- *                       the batch workspace of the context. */
+ *                       the batch workspace of the context.
+ *   LQ_OPT_BATCH_PERSISTENT  0 (default): lq_solve_batch runs its iterations as CUDA graphs of
+ *                       one launch per CG pass; 1: one persistent cooperative launch per chunk
+ *                       of reliable_every iterations runs every pass of every iteration, with
+ *                       device-wide barriers between the passes.  The barrier waits are
+ *                       bounded (about one second); a wait that runs out makes the call
+ *                       return LQ_ERR_TIMEOUT and leaves the context usable.
+ *   LQ_OPT_BATCH_BARRIER_TEST  0 (default); 1: the persistent iteration's barrier also waits for
+ *                       one block that does not exist, so every wait runs out: exercises the
+ *                       LQ_ERR_TIMEOUT path (tests of the failure detection only). */
 enum { LQ_OPT_CUDA_GRAPHS = 1, LQ_OPT_DF64_UPDATES = 2, LQ_OPT_PAIR_SITES = 3, LQ_OPT_STAGED = 4,
-       LQ_OPT_BATCH_RHS_PER_THREAD = 5 };
+       LQ_OPT_BATCH_RHS_PER_THREAD = 5, LQ_OPT_BATCH_PERSISTENT = 6, LQ_OPT_BATCH_BARRIER_TEST = 7 };
 lq_status lq_set_option(lq_ctx* ctx, int option, int value);
 
 /* Number of lattice sites V. */

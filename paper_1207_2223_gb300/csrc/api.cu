@@ -646,6 +646,11 @@ lq_status lq_set_option(lq_ctx* c, int option, int value) {
       c->batch_rb = value;
       if (c->batch) { destroy_batch_work(c->batch); c->batch = nullptr; }
       return LQ_OK;
+    case LQ_OPT_BATCH_PERSISTENT: c->batch_persistent = value ? 1 : 0; return LQ_OK;
+    case LQ_OPT_BATCH_BARRIER_TEST:
+      if (value < 0 || value > 1) return fail(c, LQ_ERR_ARG, "barrier test option is 0 or 1");
+      c->batch_barrier_extra = value;
+      return LQ_OK;
     default: return fail(c, LQ_ERR_ARG, "unknown option");
   }
 }

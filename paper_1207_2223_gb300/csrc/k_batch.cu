@@ -174,6 +174,8 @@ struct BatchWork {
   int hist_cap = 0;
   Tuning tune;
   std::vector<double> tune_ms;    // timing of every candidate (for the caller's report)
+  double* part = nullptr;         // persistent iteration: [2][kMaxCols][max_blocks] column sums
+  unsigned int* bar = nullptr;    // persistent iteration: barrier arrivals, generation
   // recorded iteration graphs with the descriptor they were recorded for
   std::vector<std::pair<BatchDesc, cudaGraphExec_t>> graphs;
 };
@@ -200,6 +202,8 @@ void free_batch(BatchWork* w) {
   if (w->br.partials) cudaFree(w->br.partials);
   if (w->br.ticket) cudaFree(w->br.ticket);
   if (w->hist) cudaFree(w->hist);
+  if (w->part) cudaFree(w->part);
+  if (w->bar) cudaFree(w->bar);
   delete w;
 }
 
@@ -374,6 +378,9 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
     ok = ok && cudaMemset(w->br.ticket, 0, sizeof(unsigned int)) == cudaSuccess;
     ok = ok && cudaMalloc(&w->st, sizeof(BatchState)) == cudaSuccess;
     ok = ok && cudaMallocHost(&w->st_host, sizeof(BatchState)) == cudaSuccess;
+    ok = ok && cudaMalloc(&w->part, sizeof(double) * 2 * kMaxCols * w->max_blocks) == cudaSuccess;
+    ok = ok && cudaMalloc(&w->bar, sizeof(unsigned int) * 2) == cudaSuccess;
+    ok = ok && cudaMemset(w->bar, 0, sizeof(unsigned int) * 2) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       free_batch(w);
@@ -425,6 +432,15 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
           }
     BatchDesc bd0 = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, cand[0].tile, cand[0].rb);
     batch_init(w, bd0, inner_prec, st);
+    // a state that never halts (no tolerance, no reliable-update trigger, no limit), reset
+    // before every candidate, so that every candidate times full iterations
+    BatchState ht = h;
+    ht.stop2 = 0.0;
+    ht.delta2 = 0.0;
+    ht.ru_every = 0;
+    ht.maxiter = 0x7fffffff;
+    ht.hist = nullptr;
+    ht.hist_len = 0;
     float best = 1e30f;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
@@ -432,6 +448,19 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
     w->tune_ms.clear();
     for (const Tuning& t : cand) {
       BatchDesc bd = make_desc(ctxs, n, nrhs, phi, x, kappa, inner_prec, t.tile, t.rb);
+      // keep the per-column scalars the initialisation computed, clear the halt controls
+      cudaMemcpyAsync(w->st_host, w->st, sizeof(BatchState), cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+      w->st_host->stop2 = ht.stop2;
+      w->st_host->delta2 = ht.delta2;
+      w->st_host->ru_every = ht.ru_every;
+      w->st_host->maxiter = ht.maxiter;
+      w->st_host->halt = 0;
+      w->st_host->iter = 0;
+      w->st_host->iter_since_ru = 0;
+      w->st_host->hist = nullptr;
+      w->st_host->hist_len = 0;
+      cudaMemcpyAsync(w->st, w->st_host, sizeof(BatchState), cudaMemcpyHostToDevice, st);
       batch_iteration_prec(w, bd, inner_prec, t, st);   // warm-up
       cudaEventRecord(a, st);
       for (int i = 0; i < 3; ++i) batch_iteration_prec(w, bd, inner_prec, t, st);
@@ -460,6 +489,29 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
   lq_status result = LQ_OK;
   cudaError_t err = cudaSuccess;
   for (long guard = 0; guard < (long)maxiter + 64; ++guard) {
+    if (c->batch_persistent) {
+      // one cooperative launch for the chunk: the three passes of every iteration with
+      // device-wide barriers in between, no per-pass launches
+      err = cudaMemsetAsync(w->bar, 0, sizeof(unsigned int), st);     // arrivals (the generation runs on)
+      if (err != cudaSuccess) break;
+      PersistArgs pa{w->plo.ref(), w->tlo.ref(), w->rlo.ref(), w->xlo.ref(), w->st, w->part, w->max_blocks,
+                     w->bar, w->bar + 1, c->batch_barrier_extra, chunk, 2000000000LL};
+      switch (inner_prec) {
+        case LQ_F16_12: case LQ_BF16_12: err = batch_persistent_h16(bd, pa, inner_prec, w->sms, w->max_blocks, st); break;
+        case LQ_I16_12: err = batch_persistent_i16(bd, pa, inner_prec, w->sms, w->max_blocks, st); break;
+        default: err = batch_persistent_f32(bd, pa, inner_prec, w->sms, w->max_blocks, st); break;
+      }
+      if (err != cudaSuccess) break;
+      s.kernel_launches += 1;
+      // a wait that gave up: the state says so; stop before the reliable update
+      err = cudaMemcpyAsync(w->st_host, w->st, sizeof(BatchState), cudaMemcpyDeviceToHost, st);
+      if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+      if (err != cudaSuccess) break;
+      if (w->st_host->timeout) {
+        result = fail(LQ_ERR_TIMEOUT, "a device-wide barrier of the persistent iteration timed out");
+        break;
+      }
+    } else {
     cudaGraphExec_t exec = nullptr;
     for (auto& gr : w->graphs)
       if (same_iteration_desc(gr.first, bd)) exec = gr.second;
@@ -484,6 +536,7 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
     err = cudaGraphLaunch(exec, st);
     if (err != cudaSuccess) break;
     s.kernel_launches += 3 * chunk;
+    }
     // reliable update: fold x, FP64 true residual per column, freeze converged columns
     batch_reliable_tail(w, bd, bd64, inner_prec, st);
     s.kernel_launches += 4;

@@ -41,7 +41,8 @@ struct BatchState {
   int conv_iter[kMaxCols];
   double stop2;            // tol^2
   double delta2;           // reliable update once a column's |r|^2 fell below delta2 * rr_ref
-  int iter, iter_since_ru, ru_every, maxiter, halt, breakdown, hist_len, pad_;
+  int iter, iter_since_ru, ru_every, maxiter, halt, breakdown, hist_len;
+  int timeout;             // a bounded wait of the persistent iteration gave up
   double* hist;            // [ncols][hist_len] relative iterated residuals
 };
 
@@ -252,7 +253,7 @@ struct BEpiResidual {                        // r64 = phi - M^dag tmp, r_lo = r6
 // Both hops of direction MU at site s for RB right-hand sides: the links
 // U_mu(s) and U_mu(s - mu) are loaded and decoded once each and applied to the
 // RB neighbour spinors (column r0 + j at element e0 + j V + n).
-template <int MU, bool DAG, GStore G, SStore SI, typename T, int RB>
+template <int MU, bool DAG, GStore G, SStore SI, typename T, int RB, int LD = 1>
 __device__ __forceinline__ void batch_hops(const Geom& geo, int total, const GaugeRef& U, const SpinorRef& in, int s,
                                            const int c[4], int e0, cplx<T> (&acc)[RB][12]) {
   constexpr int SF = DAG ? +1 : -1;
@@ -266,7 +267,7 @@ __device__ __forceinline__ void batch_hops(const Geom& geo, int total, const Gau
 #pragma unroll
     for (int j = 0; j < RB; ++j) {
       cplx<T> p[12];
-      T sc = load_spinor_raw<SI, T>(in, total, e0 + j * geo.V + n, p);
+      T sc = load_spinor_raw<SI, T, LD>(in, total, e0 + j * geo.V + n, p);
       cplx<T> h0[3], h1[3];
       project<MU, SF>(p, h0, h1);
       if (flip) sc = -sc;
@@ -290,7 +291,7 @@ __device__ __forceinline__ void batch_hops(const Geom& geo, int total, const Gau
 #pragma unroll
     for (int j = 0; j < RB; ++j) {
       cplx<T> p[12];
-      T sc = load_spinor_raw<SI, T>(in, total, e0 + j * geo.V + n, p);
+      T sc = load_spinor_raw<SI, T, LD>(in, total, e0 + j * geo.V + n, p);
       cplx<T> h0[3], h1[3];
       project<MU, -SF>(p, h0, h1);
       if (flip) sc = -sc;
@@ -312,14 +313,12 @@ __device__ __forceinline__ void batch_hops(const Geom& geo, int total, const Gau
 template <typename T, int RB> struct BatchMinBlocks { static constexpr int value = (RB == 1) ? 2 : 1; };
 template <int RB> struct BatchMinBlocks<double, RB> { static constexpr int value = 1; };
 
-template <typename T, GStore G, SStore SI, bool DAG, int RB, class Epi>
-__global__ void __launch_bounds__(256, (BatchMinBlocks<T, RB>::value))
-    batch_dslash_kernel(BatchDesc bd, SpinorRef in, Epi epi, BatchReduce br, int use64) {
-  if (epi.halted()) return;
-  __shared__ double sh_col[kMaxCols];
-  __shared__ double sh_red[RB * 32];
-  for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) sh_col[c] = 0.0;
-  __syncthreads();
+// One stencil pass over the block's tiles: out = M in (or M^dag in) per right-hand side,
+// handed to the epilogue; with Epi::REDUCE the block's per-column sums are added to
+// sh_col (block-uniform calls: every thread of the block runs the same tiles).
+template <typename T, GStore G, SStore SI, bool DAG, int RB, class Epi, int LD = 1>
+__device__ __forceinline__ void batch_stencil_pass(const BatchDesc& bd, const SpinorRef& in, const Epi& epi,
+                                                   int use64, double* sh_red, double* sh_col) {
   int cur = -1;                       // first column of the group the sums belong to
   double red[RB];
 #pragma unroll
@@ -347,16 +346,16 @@ __global__ void __launch_bounds__(256, (BatchMinBlocks<T, RB>::value))
       for (int j = 0; j < RB; ++j)
 #pragma unroll
         for (int q = 0; q < 12; ++q) acc[j][q] = {(T)0, (T)0};
-      batch_hops<0, DAG, G, SI, T, RB>(sd.geo, bd.total, U, in, s, c, e0, acc);
-      batch_hops<1, DAG, G, SI, T, RB>(sd.geo, bd.total, U, in, s, c, e0, acc);
-      batch_hops<2, DAG, G, SI, T, RB>(sd.geo, bd.total, U, in, s, c, e0, acc);
-      batch_hops<3, DAG, G, SI, T, RB>(sd.geo, bd.total, U, in, s, c, e0, acc);
+      batch_hops<0, DAG, G, SI, T, RB, LD>(sd.geo, bd.total, U, in, s, c, e0, acc);
+      batch_hops<1, DAG, G, SI, T, RB, LD>(sd.geo, bd.total, U, in, s, c, e0, acc);
+      batch_hops<2, DAG, G, SI, T, RB, LD>(sd.geo, bd.total, U, in, s, c, e0, acc);
+      batch_hops<3, DAG, G, SI, T, RB, LD>(sd.geo, bd.total, U, in, s, c, e0, acc);
       const T kappa = (T)sd.kappa;
 #pragma unroll
       for (int j = 0; j < RB; ++j) {
         const int e = e0 + j * sd.geo.V + s;
         cplx<T> ctr[12];
-        load_spinor<SI, T>(in, bd.total, e, ctr);
+        load_spinor<SI, T, LD>(in, bd.total, e, ctr);
 #pragma unroll
         for (int q = 0; q < 12; ++q) {
           acc[j][q].re = fma(-kappa, acc[j][q].re, ctr[q].re);
@@ -368,8 +367,251 @@ __global__ void __launch_bounds__(256, (BatchMinBlocks<T, RB>::value))
   }
   if constexpr (Epi::REDUCE) {
     if (cur >= 0) flush_columns<RB>(red, cur, sh_red, sh_col);
+  }
+}
+
+template <typename T, GStore G, SStore SI, bool DAG, int RB, class Epi>
+__global__ void __launch_bounds__(256, (BatchMinBlocks<T, RB>::value))
+    batch_dslash_kernel(BatchDesc bd, SpinorRef in, Epi epi, BatchReduce br, int use64) {
+  if (epi.halted()) return;
+  __shared__ double sh_col[kMaxCols];
+  __shared__ double sh_red[RB * 32];
+  for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) sh_col[c] = 0.0;
+  __syncthreads();
+  batch_stencil_pass<T, G, SI, DAG, RB>(bd, in, epi, use64, sh_red, sh_col);
+  if constexpr (Epi::REDUCE) {
     auto fin = [&](const double* tot) { epi.finalize_cols(tot, bd.ncols); };
     batch_grid_sum(bd, sh_col, br, fin);
+  }
+}
+
+// ------------------------------------------------------ persistent iteration
+// One cooperative launch runs up to max_iters CG iterations of the batch: the three
+// passes with a device-wide barrier after each.  Every block reads the per-block
+// column sums of a pass in block order and derives alpha, beta and the halt decision
+// itself, so all blocks take the same decision (deterministic, no broadcast needed);
+// block 0 writes the solver state back for the host.  Barrier waits are bounded: past
+// spin_cycles a block gives up, raises st->timeout and st->halt and returns, and every
+// other block then leaves at its next wait.
+struct PersistArgs {
+  SpinorRef plo, tlo, rlo, xlo;
+  BatchState* st;
+  double* part;                 // [2][kMaxCols][stride] per-block column sums of passes 1 and 2
+  int stride;                   // >= gridDim.x
+  unsigned int* bar_count;      // arrivals at the current barrier (0 at launch)
+  unsigned int* bar_gen;        // barrier generation
+  int bar_extra;                // blocks the barrier also waits for that do not exist (timeout tests)
+  int max_iters;
+  long long spin_cycles;        // wait limit of one barrier, in SM clock cycles
+};
+
+// CG step 2 with alpha from the block's shared memory (persistent iteration).
+template <SStore S>
+struct PEpiCG2 {
+  SpinorRef r, x, p;
+  int total;
+  const double* alpha;          // [ncols], shared memory
+  static constexpr bool REDUCE = true;
+  template <typename T> __device__ double apply(int e, int col, const cplx<T> v[12]) const {
+    const T al = (T)alpha[col];
+    cplx<T> rv[12], xv[12], pv[12];
+    load_spinor<S, T, 2>(r, total, e, rv);
+    load_spinor<xlo_store(S), T, 2>(x, total, e, xv);
+    load_spinor<S, T, 2>(p, total, e, pv);
+    T a = (T)0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      rv[k].re = fma(-al, v[k].re, rv[k].re);
+      rv[k].im = fma(-al, v[k].im, rv[k].im);
+      xv[k].re = fma(al, pv[k].re, xv[k].re);
+      xv[k].im = fma(al, pv[k].im, xv[k].im);
+      a = fma(rv[k].re, rv[k].re, a);
+      a = fma(rv[k].im, rv[k].im, a);
+    }
+    store_spinor<S, T>(r, total, e, rv);
+    store_spinor<xlo_store(S), T>(x, total, e, xv);
+    return (double)a;
+  }
+};
+
+// CG step 1 without the halt check (persistent iteration).
+template <SStore S>
+struct PEpiCG1 {
+  SpinorRef t;
+  int total;
+  static constexpr bool REDUCE = true;
+  template <typename T> __device__ double apply(int e, int, const cplx<T> v[12]) const {
+    store_spinor<S, T>(t, total, e, v);
+    T a = (T)0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) { a = fma(v[k].re, v[k].re, a); a = fma(v[k].im, v[k].im, a); }
+    return (double)a;
+  }
+};
+
+// Device-wide barrier with a bounded wait; false when this block gave up (or another did).
+__device__ __forceinline__ bool grid_barrier(const PersistArgs& a, unsigned int& gen, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *s_ok = 1;
+    __threadfence();
+    const unsigned int target = gridDim.x + (unsigned int)a.bar_extra;
+    if (atomicAdd(a.bar_count, 1u) == target - 1) {
+      atomicExch(a.bar_count, 0u);
+      __threadfence();
+      atomicAdd(a.bar_gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (atomicAdd(a.bar_gen, 0u) == gen) {
+        if (*(volatile int*)&a.st->timeout) { *s_ok = 0; break; }
+        if (clock64() - t0 > a.spin_cycles) {
+          atomicExch(&a.st->timeout, 1);
+          atomicExch(&a.st->halt, 1);
+          *s_ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  gen += 1;
+  return *s_ok != 0;
+}
+
+// Column totals of one pass: warp w sums columns w, w + nwarps, ...; lane l adds blocks
+// l, l + 32, ... and the warp adds the lanes in a fixed tree: the same in every block.
+__device__ __forceinline__ void column_totals(const double* part, int stride, int ncols, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < ncols; c += nw) {
+    double x = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) x += __ldcg(part + (size_t)c * stride + b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) out[c] = x;
+  }
+}
+
+template <GStore G, SStore S, int RB>
+__global__ void __launch_bounds__(256, (BatchMinBlocks<float, RB>::value))
+    batch_persistent_kernel(BatchDesc bd, PersistArgs a) {
+  __shared__ double sh_col[kMaxCols], sh_red[RB * 32];
+  __shared__ double s_rr[kMaxCols], s_alpha[kMaxCols], s_beta[kMaxCols], s_tot[kMaxCols];
+  __shared__ int s_ok, s_gen;
+  BatchState* st = a.st;
+  if (*(volatile int*)&st->halt) return;
+  if (threadIdx.x == 0) s_gen = (int)atomicAdd(a.bar_gen, 0u);
+  for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) s_rr[c] = st->rr[c];
+  __syncthreads();
+  unsigned int gen = (unsigned int)s_gen;
+  int iter = st->iter, since = st->iter_since_ru;
+  double* part1 = a.part;
+  double* part2 = a.part + (size_t)kMaxCols * a.stride;
+  for (int it = 0; it < a.max_iters; ++it) {
+    // pass 1: t = M p, |t|^2 per column -> alpha
+    for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) sh_col[c] = 0.0;
+    __syncthreads();
+    PEpiCG1<S> e1{a.tlo, bd.total};
+    batch_stencil_pass<float, G, S, false, RB, PEpiCG1<S>, 2>(bd, a.plo, e1, 0, sh_red, sh_col);
+    __syncthreads();
+    for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) part1[(size_t)c * a.stride + blockIdx.x] = sh_col[c];
+    if (!grid_barrier(a, gen, &s_ok)) return;
+    column_totals(part1, a.stride, bd.ncols, s_tot);
+    __syncthreads();
+    int bad = 0;
+    if (threadIdx.x < bd.ncols) {
+      const int c = threadIdx.x;
+      const double tt = s_tot[c];
+      if (st->done[c]) s_alpha[c] = 0.0;
+      else if (!(tt > 0.0) || !isfinite(tt) || !isfinite(s_rr[c])) { s_alpha[c] = 0.0; bad = 1; }
+      else s_alpha[c] = s_rr[c] / tt;
+      if (blockIdx.x == 0) st->alpha[c] = s_alpha[c];
+    }
+    if (__syncthreads_or(bad)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) { st->breakdown = 1; st->halt = 1; st->iter = iter; }
+      return;
+    }
+    // pass 2: r -= alpha M^dag t, x += alpha p, |r|^2 per column -> beta, halt decision
+    for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) sh_col[c] = 0.0;
+    __syncthreads();
+    PEpiCG2<S> e2{a.rlo, a.xlo, a.plo, bd.total, s_alpha};
+    batch_stencil_pass<float, G, S, true, RB, PEpiCG2<S>, 2>(bd, a.tlo, e2, 0, sh_red, sh_col);
+    __syncthreads();
+    for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) part2[(size_t)c * a.stride + blockIdx.x] = sh_col[c];
+    if (!grid_barrier(a, gen, &s_ok)) return;
+    column_totals(part2, a.stride, bd.ncols, s_tot);
+    __syncthreads();
+    int above = 0, trigger = 0, nonfinite = 0;
+    if (threadIdx.x < bd.ncols) {
+      const int c = threadIdx.x;
+      const double rr_new = s_tot[c];
+      if (blockIdx.x == 0 && st->hist && iter < st->hist_len)
+        st->hist[(size_t)c * st->hist_len + iter] = sqrt(rr_new / st->phi2[c]);
+      if (st->done[c]) {
+        s_beta[c] = 0.0;
+      } else {
+        if (!isfinite(rr_new)) nonfinite = 1;
+        s_beta[c] = rr_new / s_rr[c];
+        if (blockIdx.x == 0) { st->rr_prev[c] = s_rr[c]; st->rr[c] = rr_new; st->beta[c] = s_beta[c]; }
+        if (rr_new > st->stop2 * st->phi2[c]) above = 1;
+        if (rr_new < st->delta2 * st->rr_ref[c]) trigger = 1;
+      }
+    }
+    // every thread reads the column's old value before any writes the new one
+    __syncthreads();
+    if (threadIdx.x < bd.ncols && !st->done[threadIdx.x]) s_rr[threadIdx.x] = s_tot[threadIdx.x];
+    const int any_above = __syncthreads_or(above);
+    const int any_trigger = __syncthreads_or(trigger);
+    const int any_nonfinite = __syncthreads_or(nonfinite);
+    iter += 1;
+    since += 1;
+    const bool halt = !any_above || any_trigger || any_nonfinite || (st->ru_every > 0 && since >= st->ru_every) ||
+                      iter >= st->maxiter;
+    if (halt || it == a.max_iters - 1) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->iter = iter;
+        st->iter_since_ru = since;
+        if (any_nonfinite) st->breakdown = 1;
+        if (halt) st->halt = 1;
+      }
+      if (halt) return;
+    }
+    // pass 3: p = r + beta p
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < bd.total; e += gridDim.x * blockDim.x) {
+      const SysDesc& sd = bd.sys[system_of_element(bd, e)];
+      const float beta = (float)s_beta[sd.col + (e - sd.off) / sd.geo.V];
+      cplx<float> rv[12], pv[12];
+      load_spinor<S, float, 2>(a.rlo, bd.total, e, rv);
+      load_spinor<S, float, 2>(a.plo, bd.total, e, pv);
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        pv[q].re = fmaf(beta, pv[q].re, rv[q].re);
+        pv[q].im = fmaf(beta, pv[q].im, rv[q].im);
+      }
+      store_spinor<S, float>(a.plo, bd.total, e, pv);
+    }
+    if (!grid_barrier(a, gen, &s_ok)) return;
+  }
+}
+
+// Cooperative launch of the persistent iteration (grid: resident blocks, at most max_grid).
+template <GStore G, SStore S>
+cudaError_t launch_batch_persistent_t(const BatchDesc& bd, PersistArgs a, int sms, int max_grid, cudaStream_t st) {
+  auto pick = [&](auto kern) -> cudaError_t {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bd.tile, 0);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(std::min(bd.ntiles, max_grid), std::max(1, per_sm) * sms));
+    if (grid > a.stride) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&bd, (void*)&a};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kern), dim3(grid), dim3(bd.tile), args, 0, st);
+  };
+  switch (bd.rb) {
+    case 2: return pick(&batch_persistent_kernel<G, S, 2>);
+    case 3: return pick(&batch_persistent_kernel<G, S, 3>);
+    case 4: return pick(&batch_persistent_kernel<G, S, 4>);
+    default: return pick(&batch_persistent_kernel<G, S, 1>);
   }
 }
 
@@ -419,6 +661,13 @@ void launch_batch_xpay(const BatchDesc& bd, SStore s, SpinorRef r, SpinorRef p, 
 void batch_iteration_f32(const BatchIterArgs& a, const BatchDesc& bd, int prec, cudaStream_t st);
 void batch_iteration_h16(const BatchIterArgs& a, const BatchDesc& bd, int prec, cudaStream_t st);
 void batch_iteration_i16(const BatchIterArgs& a, const BatchDesc& bd, int prec, cudaStream_t st);
+// The persistent form of the same iterations (one cooperative launch), per format family.
+cudaError_t batch_persistent_f32(const BatchDesc& bd, const PersistArgs& a, int prec, int sms, int max_grid,
+                                 cudaStream_t st);
+cudaError_t batch_persistent_h16(const BatchDesc& bd, const PersistArgs& a, int prec, int sms, int max_grid,
+                                 cudaStream_t st);
+cudaError_t batch_persistent_i16(const BatchDesc& bd, const PersistArgs& a, int prec, int sms, int max_grid,
+                                 cudaStream_t st);
 
 template <GStore G, SStore S>
 void batch_iteration_t(const BatchIterArgs& a, const BatchDesc& bd, cudaStream_t st) {

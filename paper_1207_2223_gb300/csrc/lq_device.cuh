@@ -140,13 +140,18 @@ template <> struct SpinorTraits<SStore::DF64> { using half_t = void; };
 template <> struct SpinorTraits<SStore::I16> { using half_t = void; };
 
 // ----------------------------------------------------------- spinor I/O
-// RO = true: the field is read-only for the whole kernel, so loads may use
-// the non-coherent read-only path; fields a kernel also writes use RO = false.
-template <bool RO, typename W> __device__ __forceinline__ W ld(const W* p) {
-  if constexpr (RO) return __ldg(p); else return *p;
+// Load path of a field:
+//   1 (true)   read-only for the whole kernel: the non-coherent read-only path
+//   0 (false)  a field the kernel also writes (each element by the thread that reads it)
+//   2          written by other blocks of the same kernel before a device-wide barrier
+//              (persistent kernels): L2 only, never a stale L1 line
+template <int RO, typename W> __device__ __forceinline__ W ld(const W* p) {
+  if constexpr (RO == 1) return __ldg(p);
+  else if constexpr (RO == 2) return __ldcg(p);
+  else return *p;
 }
 
-template <SStore S, typename T, bool RO = true>
+template <SStore S, typename T, int RO = 1>
 __device__ __forceinline__ void load_spinor(const SpinorRef& f, int V, int s, cplx<T> v[12]) {
   if constexpr (S == SStore::DF64) {
     const float4* p = static_cast<const float4*>(f.p);
@@ -197,17 +202,17 @@ __device__ __forceinline__ void load_spinor(const SpinorRef& f, int V, int s, cp
 // Load without applying the per-site norm of 16-bit formats; returns the
 // norm (1 for FP32 / FP64).  The stencil applies it to the projected half
 // spinor, half as many multiplications as scaling all 24 reals.
-template <SStore S, typename T>
+template <SStore S, typename T, int RO = 1>
 __device__ __forceinline__ T load_spinor_raw(const SpinorRef& f, int V, int s, cplx<T> v[12]) {
   if constexpr (S == SStore::F64 || S == SStore::F32 || S == SStore::DF64) {
-    load_spinor<S, T>(f, V, s, v);
+    load_spinor<S, T, RO>(f, V, s, v);
     return (T)1;
   } else if constexpr (S == SStore::I16) {
     const uint4* p = static_cast<const uint4*>(f.p);
-    const float nrm = __ldg(f.norm + s);
+    const float nrm = ld<RO>(f.norm + s);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      uint4 w = __ldg(p + (size_t)k * V + s);
+      uint4 w = ld<RO>(p + (size_t)k * V + s);
       float2 a = q16_to2(w.x), b = q16_to2(w.y), c = q16_to2(w.z), e = q16_to2(w.w);
       v[4 * k + 0] = {(T)a.x, (T)a.y};
       v[4 * k + 1] = {(T)b.x, (T)b.y};
@@ -218,10 +223,10 @@ __device__ __forceinline__ T load_spinor_raw(const SpinorRef& f, int V, int s, c
   } else {
     using H = typename SpinorTraits<S>::half_t;
     const uint4* p = static_cast<const uint4*>(f.p);
-    const float nrm = __ldg(f.norm + s);
+    const float nrm = ld<RO>(f.norm + s);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      uint4 w = __ldg(p + (size_t)k * V + s);
+      uint4 w = ld<RO>(p + (size_t)k * V + s);
       float2 a = HalfOps<H>::to2(w.x), b = HalfOps<H>::to2(w.y), c = HalfOps<H>::to2(w.z), e = HalfOps<H>::to2(w.w);
       v[4 * k + 0] = {(T)a.x, (T)a.y};
       v[4 * k + 1] = {(T)b.x, (T)b.y};

@@ -112,6 +112,8 @@ struct lq_ctx {
   int pair_sites = 0;                    // two-site packed stencil for 16-bit storage (lq_set_option)
   int staged = 0;                        // links shared in-block through shared memory (lq_set_option)
   int batch_rb = 0;                      // batched solves: right-hand sides per thread (0: autotuned)
+  int batch_persistent = 0;              // batched solves: one cooperative launch per chunk of iterations
+  int batch_barrier_extra = 0;           // batched solves: phantom blocks the barrier waits for (timeout tests)
 };
 
 namespace lq {

@@ -15,7 +15,8 @@
 // L_x dividing TILE every x hop and all but one row of y hops stay inside
 // the tile; z and t hops, and hops that leave the tile, go through global
 // memory as in the plain kernel.  Results equal the plain kernel's up to the
-// order of the FP32 additions.
+// order of the FP32 additions.  (Measured on GB300 at 32^3 x 64, 16-bit storage:
+// slower than the plain kernel; the option stays off by default.)
 #pragma once
 
 #include "lq_dslash.cuh"
@@ -145,12 +146,17 @@ __device__ __forceinline__ void staged_second_half(const Geom& geo, const GaugeR
   }
 }
 
-// Grid-stride over tiles (one wave of resident blocks); two barriers per tile.
+// Grid-stride over tiles (one wave of resident blocks).  Two shared-memory buffers
+// alternate between consecutive tiles of a block, so one barrier per tile suffices:
+// a buffer is written again only two tiles later, after every thread has passed the
+// barrier of the tile in between and so has finished reading it.
 template <typename T, GStore G, SStore SI, bool DAG, class Epi>
 __global__ void __launch_bounds__(kStagedTile, (EpiMinBlocks<T, Epi>::value))
     dslash_staged_kernel(Geom geo, GaugeRef U, SpinorRef in, T kappa, Epi epi, ReduceScratch rs) {
   if (epi.halted()) return;
-  __shared__ StagedSmem sm;
+  extern __shared__ float4 staged_dyn[];
+  StagedSmem* bufs = reinterpret_cast<StagedSmem*>(staged_dyn);
+  int parity = 0;
   double red[Epi::NRED];
 #pragma unroll
   for (int q = 0; q < Epi::NRED; ++q) red[q] = 0.0;
@@ -160,6 +166,8 @@ __global__ void __launch_bounds__(kStagedTile, (EpiMinBlocks<T, Epi>::value))
     const int end = min(base + kStagedTile, geo.V);
     const int s = base + (int)threadIdx.x;
     const bool valid = s < geo.V;
+    StagedSmem& sm = bufs[parity];
+    parity ^= 1;
     int c[4] = {0, 0, 0, 0};
     cplx<T> acc[12];
 #pragma unroll
@@ -187,7 +195,6 @@ __global__ void __launch_bounds__(kStagedTile, (EpiMinBlocks<T, Epi>::value))
       }
       epi.apply(geo.V, s, acc, red);
     }
-    __syncthreads();
   }
   if constexpr (Epi::REDUCE) {
     double tot[Epi::NRED];
@@ -195,13 +202,27 @@ __global__ void __launch_bounds__(kStagedTile, (EpiMinBlocks<T, Epi>::value))
   }
 }
 
+constexpr size_t kStagedSmemBytes = 2 * sizeof(StagedSmem);   // 48 KiB: opted in below
+
+// Resident blocks of the staged kernel with its dynamic shared memory (once per kernel).
+template <typename T, GStore G, SStore SI, bool DAG, class Epi>
+int staged_wave() {
+  auto kern = &dslash_staged_kernel<T, G, SI, DAG, Epi>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStagedSmemBytes);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kStagedTile, kStagedSmemBytes);
+  return (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+}
+
 template <typename T, GStore G, SStore SI, bool DAG, class Epi>
 inline void launch_dslash_staged(const Geom& geo, GaugeRef U, SpinorRef in, double kappa, const Epi& epi,
                                  const ReduceScratch& rs, cudaStream_t stream) {
-  static const int wave =
-      resident_grid(reinterpret_cast<const void*>(&dslash_staged_kernel<T, G, SI, DAG, Epi>), kStagedTile);
+  static const int wave = staged_wave<T, G, SI, DAG, Epi>();
   const int grid = std::min(grid_for(geo.V, kStagedTile), wave);
-  dslash_staged_kernel<T, G, SI, DAG, Epi><<<grid, kStagedTile, 0, stream>>>(geo, U, in, (T)kappa, epi, rs);
+  dslash_staged_kernel<T, G, SI, DAG, Epi><<<grid, kStagedTile, kStagedSmemBytes, stream>>>(geo, U, in, (T)kappa,
+                                                                                            epi, rs);
 }
 
 }  // namespace lq

@@ -13,7 +13,7 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblq.so")
 
-LQ_OK, LQ_ERR_ARG, LQ_ERR_SHAPE, LQ_ERR_CUDA, LQ_ERR_NOT_CONVERGED, LQ_ERR_NAN, LQ_ERR_STATE = range(7)
+LQ_OK, LQ_ERR_ARG, LQ_ERR_SHAPE, LQ_ERR_CUDA, LQ_ERR_NOT_CONVERGED, LQ_ERR_NAN, LQ_ERR_STATE, LQ_ERR_TIMEOUT = range(8)
 LQ_F64, LQ_F32, LQ_F32_12, LQ_F16_12, LQ_BF16_12, LQ_DF64, LQ_I16_12 = range(7)
 PRECISIONS = {"f64": LQ_F64, "f32": LQ_F32, "f32_12": LQ_F32_12, "f16_12": LQ_F16_12, "bf16_12": LQ_BF16_12,
               "df64": LQ_DF64, "i16_12": LQ_I16_12}
@@ -167,7 +167,8 @@ def lq_set_stream(ctx, stream):
     _check(ctx, load().lq_set_stream(ctx, stream))
 
 
-LQ_OPT_CUDA_GRAPHS, LQ_OPT_DF64_UPDATES, LQ_OPT_PAIR_SITES, LQ_OPT_STAGED, LQ_OPT_BATCH_RHS_PER_THREAD = 1, 2, 3, 4, 5
+LQ_OPT_CUDA_GRAPHS, LQ_OPT_DF64_UPDATES, LQ_OPT_PAIR_SITES, LQ_OPT_STAGED = 1, 2, 3, 4
+LQ_OPT_BATCH_RHS_PER_THREAD, LQ_OPT_BATCH_PERSISTENT, LQ_OPT_BATCH_BARRIER_TEST = 5, 6, 7
 
 
 def lq_set_option(ctx, option, value):

@@ -213,3 +213,85 @@ def test_autotuner_reports_its_choice(lq):
     # rhs per thread 1, 2, 3 divide 6 (4 does not): 3 shapes each
     assert len(t1["candidate_ms"]) == 9 and t1["rhs_per_thread"] in (1, 2, 3)
     assert min(t1["candidate_ms"]) > 0 and t1 == t2
+
+
+@pytest.mark.parametrize("prec", [2, 3, 6])
+def test_persistent_iteration_matches_graphs_and_oracle(lq, prec):
+    """One cooperative launch per chunk of iterations (all passes, device-wide barriers) gives
+    the same solutions as the per-pass launches within the conditioning bound, each column to
+    a 1e-10 FP64 true residual, for right-hand sides sharing links and for uneven lattices."""
+    dims, R, kappa = (4, 4, 4, 8), 6, 0.15
+    lat = Lattice(dims)
+    U = gauge_exp_iA(lat, 0.3, 9)
+    phis = np.stack([source(lat, 9, i) for i in range(R)])
+    sols = {}
+    for persistent in (0, 1):
+        ctx = lq.lq_create(dims)
+        try:
+            lq.lq_set_option(ctx, lq.LQ_OPT_BATCH_PERSISTENT, persistent)
+            lq.lq_gauge_set(ctx, dev(U))
+            x = torch.zeros_like(dev(phis))
+            status, st, iters, resid, hist = lq.lq_solve_batch([ctx], [x], [dev(phis)], [kappa], R, 1e-10, 5000,
+                                                               prec, 50, hist_len=2000)
+            assert status == lq.LQ_OK and np.all(resid <= 1e-10), (persistent, resid)
+            assert np.all(hist[:, :st["iterations"]].min(axis=1) < 1e-6)
+            sols[persistent] = host(x)
+        finally:
+            lq.lq_destroy(ctx)
+    assert rel_err(sols[1], sols[0]) < X_TOL
+    xr, _, _ = cg_MdagM(U, phis[3], dims, kappa, 1e-13)
+    assert rel_err(sols[1][3], xr) < X_TOL
+    # uneven lattices and kappas in one persistent launch
+    shapes = [(4, 4, 4, 4), (2, 4, 6, 4), (6, 2, 2, 4)]
+    kappas = [0.12, 0.14, 0.155]
+    ctxs, xs, ph, Us = [], [], [], []
+    try:
+        for k, d in enumerate(shapes):
+            l2 = Lattice(d)
+            Uk = gauge_exp_iA(l2, 0.3, 20 + k)
+            c = lq.lq_create(d)
+            lq.lq_gauge_set(c, dev(Uk))
+            if k == 0:
+                lq.lq_set_option(c, lq.LQ_OPT_BATCH_PERSISTENT, 1)
+            ctxs.append(c)
+            Us.append(Uk)
+            ph.append(dev(source(l2, 20 + k)))
+            xs.append(torch.zeros_like(ph[-1]))
+        status, st, iters, resid, _ = lq.lq_solve_batch(ctxs, xs, ph, kappas, 1, 1e-10, 5000, prec, 50)
+        got = [host(v) for v in xs]
+    finally:
+        for c in ctxs:
+            lq.lq_destroy(c)
+    assert status == lq.LQ_OK and np.all(resid <= 1e-10)
+    for k, d in enumerate(shapes):
+        xr, _, _ = cg_MdagM(Us[k], host(ph[k]), d, kappas[k], 1e-13)
+        assert rel_err(got[k], xr) < X_TOL, d
+
+
+def test_persistent_barrier_timeout_is_reported_and_recoverable(lq):
+    """Failure detection of the persistent iteration: with the test option its barrier waits
+    for a block that does not exist, every wait runs out after about a second, and the call
+    returns LQ_ERR_TIMEOUT instead of hanging; the context then solves normally."""
+    dims, R = (4, 4, 2, 4), 2
+    lat = Lattice(dims)
+    ctx = lq.lq_create(dims)
+    try:
+        lq.lq_gauge_set(ctx, dev(gauge_exp_iA(lat, 0.3, 4)))
+        phis = dev(np.stack([source(lat, 4, i) for i in range(R)]))
+        x = torch.zeros_like(phis)
+        lq.lq_set_option(ctx, lq.LQ_OPT_BATCH_PERSISTENT, 1)
+        lq.lq_set_option(ctx, lq.LQ_OPT_BATCH_BARRIER_TEST, 1)
+        with pytest.raises(lq.LQError) as e:
+            lq.lq_solve_batch([ctx], [x], [phis], [0.15], R, 1e-10, 5000, lq.LQ_F32_12, 50)
+        assert e.value.status == lq.LQ_ERR_TIMEOUT
+        assert "timed out" in str(e.value)
+        lq.lq_set_option(ctx, lq.LQ_OPT_BATCH_BARRIER_TEST, 0)
+        x = torch.zeros_like(phis)
+        status, st, iters, resid, _ = lq.lq_solve_batch([ctx], [x], [phis], [0.15], R, 1e-10, 5000, lq.LQ_F32_12, 50)
+        assert status == lq.LQ_OK and np.all(resid <= 1e-10)
+        # and the single solver on the same context is unaffected
+        xs = torch.zeros_like(phis[0])
+        status, st1 = lq.lq_solve_MdagM(ctx, xs, phis[0], 0.15, 1e-10, 5000, lq.LQ_F32_12, 50)
+        assert status == lq.LQ_OK
+    finally:
+        lq.lq_destroy(ctx)

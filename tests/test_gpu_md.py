@@ -169,11 +169,13 @@ def test_trajectory_mixed_precision_solves(lq, prec):
     # solution is no longer close to CG's Galerkin solution, so S_f = phi^dag X moves at
     # first order in the residual r, |X^dag r| <= |X| |r| (measured 2.9e-8 here); the
     # other formats stay within 1e-8 of the oracle
+    # (the same first-order effect moves the forces, so the final links of the BF16 run are
+    # held to 1e-9 instead of 1e-10; measured 1.1e-10)
     tol = 1e-7 if prec == 4 else 1e-8
     assert abs(r["dH"] - ref["dH"]) < tol, (prec, r["dH"], ref["dH"])
     assert bool(r["accepted"]) == ref["accept"]
     assert np.max(np.abs(pg - ref["p"])) < 1e-8
-    assert np.max(np.abs(Ug - ref["U"])) < 1e-10
+    assert np.max(np.abs(Ug - ref["U"])) < (1e-9 if prec == 4 else 1e-10)
 
 
 def test_trajectory_reject_restores_links(lq):
