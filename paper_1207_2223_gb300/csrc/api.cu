@@ -238,12 +238,21 @@ lq_status solve_internal(lq_ctx* c, double kappa, double tol, int maxiter, int i
       if (!st.halt) continue;
       // true residual; for mixed solves this is the reliable update
       if (dfru) {
-        // double-float on the FP32 pipe; a residual meeting tol is certified in FP64
-        df_reliable_update(c, kappa, inner, c->stream);
-        s.kernel_launches += 3;
-        LQ_CUDA(c, cudaGetLastError());
-        LQ_TRY(read_state(c));
-        rel = std::sqrt(c->state_host->rr_true / c->state_host->phi2);
+        // double-float on the FP32 pipe; a residual meeting tol is certified in FP64.  When
+        // the iterated residual has met tol the update is almost surely the last: it goes
+        // straight to the FP64 certification.
+        const bool last = st.rr <= st.stop2;
+        if (last) {
+          df_accumulate(c, inner, c->stream);
+          s.kernel_launches += 1;
+          rel = 0.0;
+        } else {
+          df_reliable_update(c, kappa, inner, c->stream);
+          s.kernel_launches += 3;
+          LQ_CUDA(c, cudaGetLastError());
+          LQ_TRY(read_state(c));
+          rel = std::sqrt(c->state_host->rr_true / c->state_host->phi2);
+        }
         s.reliable_updates++;
         if (std::isfinite(rel) && rel <= tol) {
           launch_convert_spinor(g, SStore::DF64, c->x_df.ref(), SStore::F64, c->x64.ref(), c->stream);

@@ -2,6 +2,7 @@
 // precision: out = M in, no reduction.
 #include "lq_internal.h"
 #include "lq_staged.cuh"
+#include "lq_dfsplit.cuh"
 
 namespace lq {
 
@@ -33,7 +34,14 @@ void apply_M_prec(const Geom& g, int prec, const void* gauge, SpinorRef in, Spin
     case LQ_F32_12: apply_one<float, GStore::F32_12, SStore::F32>(g, gauge, in, out, kappa, dagger, stream, staged); break;
     case LQ_F16_12: apply_one<float, GStore::F16_12, SStore::F16>(g, gauge, in, out, kappa, dagger, stream, staged); break;
     case LQ_BF16_12: apply_one<float, GStore::BF16_12, SStore::BF16>(g, gauge, in, out, kappa, dagger, stream, staged); break;
-    case LQ_DF64: apply_one<df64, GStore::DF64_18, SStore::DF64>(g, gauge, in, out, kappa, dagger, stream); break;
+    case LQ_DF64: {
+      // the two-threads-per-site double-float operator (lq_dfsplit.cuh)
+      DFEpiStore epi{out};
+      ReduceScratch none{nullptr, nullptr, 0};
+      if (dagger) launch_dslash_dfsplit<true>(g, gauge, in, kappa, epi, none, stream);
+      else launch_dslash_dfsplit<false>(g, gauge, in, kappa, epi, none, stream);
+      break;
+    }
     case LQ_I16_12: apply_one<float, GStore::I16_12, SStore::I16>(g, gauge, in, out, kappa, dagger, stream, staged); break;
   }
 }

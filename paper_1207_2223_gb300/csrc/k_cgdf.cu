@@ -1,39 +1,15 @@
 // Double-float reliable update of the mixed-precision CG (the CG routine of
 // Sec. 3 with the mixed precision the paper names as future work in Sec. 4):
 //   x_df += x_lo, x_lo = 0;   tmp = M x_df;   r = phi - M^dag tmp
-// with links and spinors stored as hi/lo float pairs and the arithmetic of
-// lq_df64.cuh on the FP32 pipe.  The residual goes to a double-float field
+// with links and spinors stored as hi/lo float pairs, the arithmetic of
+// lq_df64.cuh on the FP32 pipe and two threads per site (lq_dfsplit.cuh).  The residual goes to a double-float field
 // (r_df) and to the inner format (r_lo), |r|^2 to state->rr_true.
 #include "lq_internal.h"
+#include "lq_dfsplit.cuh"
 
 namespace lq {
 
 static constexpr int kBS = 256;
-
-template <SStore SLO>
-struct EpiResidualDF {
-  static constexpr int NRED = 1;
-  static constexpr bool REDUCE = true;
-  SpinorRef phi, rdf, rlo;
-  SolverState* st;
-  __device__ bool halted() const { return false; }
-  template <typename T> __device__ void apply(int V, int s, cplx<T> v[12], double (&red)[NRED]) const {
-    cplx<df64> ph[12], r[12];
-    load_spinor<SStore::DF64, df64>(phi, V, s, ph);
-    float a = 0.f;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      r[k] = {ph[k].re - to_df<T>(v[k].re), ph[k].im - to_df<T>(v[k].im)};
-      const float re = (float)r[k].re, im = (float)r[k].im;
-      a = fmaf(re, re, a);
-      a = fmaf(im, im, a);
-    }
-    store_spinor<SStore::DF64, df64>(rdf, V, s, r);
-    store_spinor<SLO, df64>(rlo, V, s, r);
-    red[0] += (double)a;
-  }
-  __device__ void finalize(double (&tot)[NRED]) const { st->rr_true = tot[0]; }
-};
 
 // x_df += x_lo; x_lo = 0
 template <SStore SLO>
@@ -73,11 +49,26 @@ static void ru(lq_ctx* c, double kappa, cudaStream_t stream) {
   const Geom& g = c->geo;
   const int k = (int)SLO;
   accumulate_df_kernel<SLO><<<grid_for(g.V, kBS), kBS, 0, stream>>>(g.V, c->x_lo[k].ref(), c->x_df.ref());
-  GaugeRef U{c->gauge_lo[LQ_DF64]};
-  EpiStore<SStore::DF64> e0{c->tmp_df.ref()};
-  launch_dslash<df64, GStore::DF64_18, SStore::DF64, false>(g, U, c->x_df.ref(), kappa, e0, c->rs, stream);
-  EpiResidualDF<SLO> e1{c->phi_df.ref(), c->r_df.ref(), c->r_lo[k].ref(), c->state};
-  launch_dslash<df64, GStore::DF64_18, SStore::DF64, true>(g, U, c->tmp_df.ref(), kappa, e1, c->rs, stream);
+  DFEpiStore e0{c->tmp_df.ref()};
+  launch_dslash_dfsplit<false>(g, c->gauge_lo[LQ_DF64], c->x_df.ref(), kappa, e0, c->rs, stream);
+  DFEpiResidual<SLO> e1{c->phi_df.ref(), c->r_df.ref(), c->r_lo[k].ref(), c->state};
+  launch_dslash_dfsplit<true>(g, c->gauge_lo[LQ_DF64], c->tmp_df.ref(), kappa, e1, c->rs, stream);
+}
+
+template <SStore SLO>
+static void acc_only(lq_ctx* c, cudaStream_t stream) {
+  const Geom& g = c->geo;
+  accumulate_df_kernel<SLO><<<grid_for(g.V, kBS), kBS, 0, stream>>>(g.V, c->x_lo[(int)SLO].ref(), c->x_df.ref());
+}
+
+void df_accumulate(lq_ctx* c, int inner_prec, cudaStream_t stream) {
+  switch (spinor_store_of(inner_prec)) {
+    case SStore::F32: acc_only<SStore::F32>(c, stream); break;
+    case SStore::F16: acc_only<SStore::F16>(c, stream); break;
+    case SStore::BF16: acc_only<SStore::BF16>(c, stream); break;
+    case SStore::I16: acc_only<SStore::I16>(c, stream); break;
+    default: break;
+  }
 }
 
 void df_reliable_update(lq_ctx* c, double kappa, int inner_prec, cudaStream_t stream) {

@@ -376,6 +376,17 @@ __device__ __forceinline__ void load_link_q16(const GaugeRef& g, int V, int mu, 
   }
 }
 
+// -x by flipping the sign bit (an integer operation: exact, and off the FP64 pipe for doubles)
+__device__ __forceinline__ double flip_sign(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+__device__ __forceinline__ float flip_sign(float x) { return __int_as_float(__float_as_int(x) ^ (int)0x80000000); }
+__device__ __forceinline__ df64 flip_sign(df64 x) { return df64(flip_sign(x.hi), flip_sign(x.lo)); }
+template <typename T> __device__ __forceinline__ void negate3(cplx<T> h[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) h[k] = {flip_sign(h[k].re), flip_sign(h[k].im)};
+}
+
 // ----------------------------------------------------- spin projection
 // Projector (1 + S gamma_mu) in the DeGrand-Rossi basis.  The projected
 // spinor has rank 2: components 0, 1 ("h0", "h1") determine 2, 3.
@@ -404,8 +415,31 @@ __device__ __forceinline__ void project(const cplx<T> p[12], cplx<T> h0[3], cplx
   }
 }
 
-template <int MU, int S, typename T>
+// INIT: the first contribution of a site sets the accumulator instead of adding to zero
+// (the same values; no additions).
+template <int MU, int S, typename T, bool INIT = false>
 __device__ __forceinline__ void accumulate(cplx<T> acc[12], const cplx<T> w0[3], const cplx<T> w1[3]) {
+  if constexpr (INIT) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc[c] = w0[c];
+      acc[3 + c] = w1[c];
+      if constexpr (MU == 0) {
+        if (S > 0) { acc[6 + c] = -times_i(w1[c]); acc[9 + c] = -times_i(w0[c]); }
+        else       { acc[6 + c] = times_i(w1[c]); acc[9 + c] = times_i(w0[c]); }
+      } else if constexpr (MU == 1) {
+        if (S > 0) { acc[6 + c] = w1[c]; acc[9 + c] = -w0[c]; }
+        else       { acc[6 + c] = -w1[c]; acc[9 + c] = w0[c]; }
+      } else if constexpr (MU == 2) {
+        if (S > 0) { acc[6 + c] = -times_i(w0[c]); acc[9 + c] = times_i(w1[c]); }
+        else       { acc[6 + c] = times_i(w0[c]); acc[9 + c] = -times_i(w1[c]); }
+      } else {
+        if (S > 0) { acc[6 + c] = w0[c]; acc[9 + c] = w1[c]; }
+        else       { acc[6 + c] = -w0[c]; acc[9 + c] = -w1[c]; }
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     acc[c] = acc[c] + w0[c];

@@ -1,0 +1,227 @@
+// Double-float Wilson operator with two threads per site (the operator of
+// Sec. 3 kernel 1 in ~48-bit double-float arithmetic on the FP32 pipe, used
+// for the intermediate true residuals of mixed-precision CG).
+//
+// Double-float values double the registers of every quantity, and the long
+// dependent chains of the compensated sums need many warps in flight.  The
+// work of a site is therefore split between a pair of adjacent lanes by the
+// rank-2 structure of the spin projection: with (1 -+ g_mu) in the
+// DeGrand-Rossi basis the projected spinor is two colour vectors h0, h1 built
+// from spins (0, 3) and (1, 2) for mu = x, y, or (0, 2) and (1, 3) for
+// mu = z, t, and U h0 feeds spin 0 and one lower spin, U h1 spin 1 and the
+// other.  Lane 0 of the pair computes everything that comes from h0, lane 1
+// everything from h1; each accumulates its upper spin and partial sums of
+// spins 2 and 3, and one exchange of partial sums at the end completes the
+// lower spins (lane 0 keeps spins 0 and 2, lane 1 spins 1 and 3).  Links are
+// read one row (U) or one column (U^dag) at a time and each row product is
+// added at once, so no thread holds a whole link.  128 registers per thread,
+// two blocks of 256 threads per SM: twice the warps of a one-thread-per-site
+// double-float stencil (a third block spills).
+#pragma once
+
+#include "lq_dslash.cuh"
+
+namespace lq {
+
+constexpr int kDFSplitBlock = 256;
+// resident blocks of 256 threads per SM requested from the compiler (register cap)
+#ifndef LQ_DFSPLIT_MIN_BLOCKS
+#define LQ_DFSPLIT_MIN_BLOCKS 2
+#endif
+
+struct DFLower {
+  cplx<df64> s2[3], s3[3];
+};
+
+__device__ __forceinline__ cplx<df64> ldf(const float4* p, size_t i) {
+  const float4 w = __ldg(p + i);
+  return {df64(w.x, w.y), df64(w.z, w.w)};
+}
+
+// One hop of lane `half` in direction MU with projector sign S (+1: 1 + g, -1: 1 - g).
+// FWD: the link U_mu(s) and the spinor at the forward neighbour; otherwise U_mu(n)^dag
+// and the spinor at the backward neighbour n.  flip: the hop crosses the antiperiodic
+// time boundary (sign -1).
+template <int MU, int S, bool FWD>
+__device__ __forceinline__ void df_hop(const float4* psi, const float4* U, int V, int n, int link_site, int half,
+                                       bool flip, cplx<df64> up[3], DFLower& lo) {
+  // spins of this lane: a (upper) and b (the partner in the projection)
+  const int a = half;
+  const int b = (MU <= 1) ? 3 - half : 2 + half;
+  cplx<df64> h[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cplx<df64> pa = ldf(psi, (size_t)(3 * a + c) * V + n);
+    const cplx<df64> pb = ldf(psi, (size_t)(3 * b + c) * V + n);
+    // h0 (half 0) / h1 (half 1) of the projector (1 + S g_mu)
+    cplx<df64> q;
+    if constexpr (MU == 0) q = times_i(pb);                                     // x: p0 + S i p3, p1 + S i p2
+    else if constexpr (MU == 1) q = (half == 0) ? -pb : pb;                     // y: p0 - S p3,   p1 + S p2
+    else if constexpr (MU == 2) q = (half == 0) ? times_i(pb) : -times_i(pb);   // z: p0 + S i p2, p1 - S i p3
+    else q = pb;                                                                // t: p0 + S p2,   p1 + S p3
+    h[c] = (S > 0) ? pa + q : pa - q;
+    if (flip) h[c] = -h[c];
+  }
+  const float4* Um = U + (size_t)MU * 9 * V;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    cplx<df64> w;
+    if constexpr (FWD) {
+      w = cmul(ldf(Um, (size_t)(3 * i) * V + link_site), h[0]);
+      w = cmadd(w, ldf(Um, (size_t)(3 * i + 1) * V + link_site), h[1]);
+      w = cmadd(w, ldf(Um, (size_t)(3 * i + 2) * V + link_site), h[2]);
+    } else {
+      w = cjmul(ldf(Um, (size_t)i * V + link_site), h[0]);
+      w = cjmadd(w, ldf(Um, (size_t)(3 + i) * V + link_site), h[1]);
+      w = cjmadd(w, ldf(Um, (size_t)(6 + i) * V + link_site), h[2]);
+    }
+    up[i] = up[i] + w;
+    // lower spins (accumulate<MU, S> of the one-thread stencil, restricted to w0 or w1)
+    if constexpr (MU == 0) {           // spin 2 += -S i w1, spin 3 += -S i w0
+      const cplx<df64> t = (S > 0) ? -times_i(w) : times_i(w);
+      if (half == 0) lo.s3[i] = lo.s3[i] + t; else lo.s2[i] = lo.s2[i] + t;
+    } else if constexpr (MU == 1) {    // spin 2 += S w1, spin 3 += -S w0
+      if (half == 0) lo.s3[i] = (S > 0) ? lo.s3[i] - w : lo.s3[i] + w;
+      else lo.s2[i] = (S > 0) ? lo.s2[i] + w : lo.s2[i] - w;
+    } else if constexpr (MU == 2) {    // spin 2 += -S i w0, spin 3 += S i w1
+      const cplx<df64> t = times_i(w);
+      if (half == 0) lo.s2[i] = (S > 0) ? lo.s2[i] - t : lo.s2[i] + t;
+      else lo.s3[i] = (S > 0) ? lo.s3[i] + t : lo.s3[i] - t;
+    } else {                           // spin 2 += S w0, spin 3 += S w1
+      if (half == 0) lo.s2[i] = (S > 0) ? lo.s2[i] + w : lo.s2[i] - w;
+      else lo.s3[i] = (S > 0) ? lo.s3[i] + w : lo.s3[i] - w;
+    }
+  }
+}
+
+template <int MU, bool DAG>
+__device__ __forceinline__ void df_dir(const Geom& geo, const float4* psi, const float4* U, int s, const int c[4],
+                                       int half, cplx<df64> up[3], DFLower& lo) {
+  constexpr int SF = DAG ? +1 : -1;
+  const int f = nbr_fwd(geo, s, c, MU);
+  df_hop<MU, SF, true>(psi, U, geo.V, f, s, half, MU == 3 && geo.antiperiodic && c[3] == geo.L[3] - 1, up, lo);
+  const int b = nbr_bwd(geo, s, c, MU);
+  df_hop<MU, -SF, false>(psi, U, geo.V, b, b, half, MU == 3 && geo.antiperiodic && c[3] == 0, up, lo);
+}
+
+__device__ __forceinline__ df64 shfl_df(df64 v) {
+  return df64(__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1));
+}
+
+// out spins of lane `half`: v[0..2] = spin half, v[3..5] = spin half + 2 (colour fastest)
+template <bool DAG, class Epi>
+__global__ void __launch_bounds__(kDFSplitBlock, LQ_DFSPLIT_MIN_BLOCKS)
+    dslash_dfsplit_kernel(Geom geo, const float4* __restrict__ U, const float4* __restrict__ psi, df64 kappa,
+                          Epi epi, ReduceScratch rs) {
+  double red[1] = {0.0};
+  const int half = threadIdx.x & 1;
+  const int Vr = (geo.V + 15) & ~15;                     // whole warps iterate together
+  const int stride = (gridDim.x * blockDim.x) >> 1;
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 1; s < Vr; s += stride) {
+    const bool active = s < geo.V;
+    const int ss = active ? s : 0;
+    int c[4];
+    site_coords(geo, ss, c);
+    cplx<df64> up[3];
+    DFLower lo;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      up[i] = {df64(0.f), df64(0.f)};
+      lo.s2[i] = up[i];
+      lo.s3[i] = up[i];
+    }
+    df_dir<0, DAG>(geo, psi, U, ss, c, half, up, lo);
+    df_dir<1, DAG>(geo, psi, U, ss, c, half, up, lo);
+    df_dir<2, DAG>(geo, psi, U, ss, c, half, up, lo);
+    df_dir<3, DAG>(geo, psi, U, ss, c, half, up, lo);
+    // lane 0 keeps spin 2 and hands its spin-3 sums to lane 1, and the other way round
+    cplx<df64> v[6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const cplx<df64> give = half == 0 ? lo.s3[i] : lo.s2[i];
+      const cplx<df64> mine = half == 0 ? lo.s2[i] : lo.s3[i];
+      const cplx<df64> got = {shfl_df(give.re), shfl_df(give.im)};
+      v[i] = up[i];
+      v[3 + i] = mine + got;
+    }
+    // M = 1 - kappa H on the lane's two spins
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int comp = (k < 3) ? 3 * half + k : 3 * (half + 2) + (k - 3);
+      const cplx<df64> ctr = ldf(psi, (size_t)comp * geo.V + ss);
+      v[k] = {fma(-kappa, v[k].re, ctr.re), fma(-kappa, v[k].im, ctr.im)};
+    }
+    epi.apply(geo.V, ss, half, active, v, red);
+  }
+  if constexpr (Epi::REDUCE) {
+    double tot[1];
+    if (grid_sum<1>(red, rs, tot)) epi.finalize(tot);
+  }
+}
+
+// ------------------------------------------------------------ epilogues
+// out = M in, double-float field
+struct DFEpiStore {
+  static constexpr bool REDUCE = false;
+  SpinorRef out;
+  __device__ void apply(int V, int s, int half, bool active, const cplx<df64> v[6], double (&)[1]) const {
+    if (!active) return;
+    float4* p = static_cast<float4*>(out.p);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int comp = (k < 3) ? 3 * half + k : 3 * (half + 2) + (k - 3);
+      p[(size_t)comp * V + s] = make_float4(v[k].re.hi, v[k].re.lo, v[k].im.hi, v[k].im.lo);
+    }
+  }
+  __device__ void finalize(double (&)[1]) const {}
+};
+
+// r = phi - M^dag tmp (double-float), r_lo = r in the inner format, rr_true = |r|^2
+template <SStore SLO>
+struct DFEpiResidual {
+  static constexpr bool REDUCE = true;
+  SpinorRef phi, rdf, rlo;
+  SolverState* st;
+  __device__ void apply(int V, int s, int half, bool active, const cplx<df64> v[6], double (&red)[1]) const {
+    const float4* ph = static_cast<const float4*>(phi.p);
+    float4* rp = static_cast<float4*>(rdf.p);
+    cplx<float> mine[6];
+    float a = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int comp = (k < 3) ? 3 * half + k : 3 * (half + 2) + (k - 3);
+      const cplx<df64> f = ldf(ph, (size_t)comp * V + s);
+      const cplx<df64> r = {f.re - v[k].re, f.im - v[k].im};
+      if (active) rp[(size_t)comp * V + s] = make_float4(r.re.hi, r.re.lo, r.im.hi, r.im.lo);
+      mine[k] = {(float)r.re, (float)r.im};
+      a = fmaf(mine[k].re, mine[k].re, a);
+      a = fmaf(mine[k].im, mine[k].im, a);
+    }
+    // the inner-format copy needs all 12 components of the site (per-site norm): lane 0 gathers
+    cplx<float> full[12];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const cplx<float> o = {__shfl_xor_sync(0xffffffffu, mine[k].re, 1), __shfl_xor_sync(0xffffffffu, mine[k].im, 1)};
+      // lane 0 holds spins 0, 2; the partner spins 1, 3
+      const int ca = (k < 3) ? k : 6 + (k - 3);        // own components (lane 0 view)
+      const int cb = (k < 3) ? 3 + k : 9 + (k - 3);    // partner's components
+      full[ca] = mine[k];
+      full[cb] = o;
+    }
+    if (active && half == 0) store_spinor<SLO, float>(rlo, V, s, full);
+    if (active) red[0] += (double)a;
+  }
+  __device__ void finalize(double (&tot)[1]) const { st->rr_true = tot[0]; }
+};
+
+template <bool DAG, class Epi>
+inline void launch_dslash_dfsplit(const Geom& geo, const void* U, SpinorRef in, double kappa, const Epi& epi,
+                                  const ReduceScratch& rs, cudaStream_t stream) {
+  static const int wave =
+      resident_grid(reinterpret_cast<const void*>(&dslash_dfsplit_kernel<DAG, Epi>), kDFSplitBlock);
+  const int grid = std::max(1, std::min(grid_for(2 * geo.V, kDFSplitBlock), wave));
+  dslash_dfsplit_kernel<DAG, Epi><<<grid, kDFSplitBlock, 0, stream>>>(
+      geo, static_cast<const float4*>(U), static_cast<const float4*>(in.p), df64(kappa), epi, rs);
+}
+
+}  // namespace lq

@@ -67,23 +67,31 @@ struct BatchIndex {
   __device__ __forceinline__ int operator()(int n) const { return off + n * R + r; }
 };
 
-template <int MU, bool DAG, GStore G, SStore SI, typename T, class IX = SingleIndex>
+// Both hops of direction MU at site s.  INIT: the forward hop is the site's first
+// contribution and sets acc (the first direction of the stencil).  The antiperiodic
+// sign of a hop across the time boundary is folded into the norm scale of 16-bit
+// storage, which is multiplied anyway; for the other formats it flips sign bits.
+template <int MU, bool DAG, GStore G, SStore SI, typename T, class IX = SingleIndex, bool INIT = false>
 __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, const SpinorRef& in, int s,
                                         const int c[4], cplx<T> acc[12], IX ix = IX{0}) {
   if constexpr (std::is_same<IX, SingleIndex>::value) ix.V = geo.V;
   constexpr int SF = DAG ? +1 : -1;   // forward hop uses (1 + SF g_mu)
+  constexpr bool SCALED = SI == SStore::F16 || SI == SStore::BF16 || SI == SStore::I16 || G == GStore::I16_12;
   {
     const int n = nbr_fwd(geo, s, c, MU);
     cplx<T> p[12];
     T sc = load_spinor_raw<SI, T>(in, ix.stride(), ix(n), p);
     cplx<T> h0[3], h1[3];
     project<MU, SF>(p, h0, h1);
-    if (MU == 3 && geo.antiperiodic && c[3] == geo.L[3] - 1) sc = -sc;
-    if constexpr (G == GStore::I16_12) sc = sc * (T)kQ16Inv;   // links as raw integers
-    if (SI == SStore::F16 || SI == SStore::BF16 || SI == SStore::I16 || G == GStore::I16_12 ||
-        (MU == 3 && geo.antiperiodic)) {
+    const bool flip = MU == 3 && geo.antiperiodic && c[3] == geo.L[3] - 1;
+    if constexpr (SCALED) {
+      if (flip) sc = -sc;
+      if constexpr (G == GStore::I16_12) sc = sc * (T)kQ16Inv;   // links as raw integers
 #pragma unroll
       for (int k = 0; k < 3; ++k) { h0[k] = scale_c(sc, h0[k]); h1[k] = scale_c(sc, h1[k]); }
+    } else if (flip) {
+      negate3(h0);
+      negate3(h1);
     }
     cplx<T> u[9];
     if constexpr (G == GStore::I16_12) load_link_q16<T>(U, geo.V, MU, s, u);
@@ -91,7 +99,7 @@ __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, cons
     cplx<T> w0[3], w1[3];
     su3_mul(u, h0, w0);
     su3_mul(u, h1, w1);
-    accumulate<MU, SF>(acc, w0, w1);
+    accumulate<MU, SF, T, INIT>(acc, w0, w1);
   }
   {
     const int n = nbr_bwd(geo, s, c, MU);
@@ -99,12 +107,15 @@ __device__ __forceinline__ void hop_dir(const Geom& geo, const GaugeRef& U, cons
     T sc = load_spinor_raw<SI, T>(in, ix.stride(), ix(n), p);
     cplx<T> h0[3], h1[3];
     project<MU, -SF>(p, h0, h1);
-    if (MU == 3 && geo.antiperiodic && c[3] == 0) sc = -sc;
-    if constexpr (G == GStore::I16_12) sc = sc * (T)kQ16Inv;   // links as raw integers
-    if (SI == SStore::F16 || SI == SStore::BF16 || SI == SStore::I16 || G == GStore::I16_12 ||
-        (MU == 3 && geo.antiperiodic)) {
+    const bool flip = MU == 3 && geo.antiperiodic && c[3] == 0;
+    if constexpr (SCALED) {
+      if (flip) sc = -sc;
+      if constexpr (G == GStore::I16_12) sc = sc * (T)kQ16Inv;   // links as raw integers
 #pragma unroll
       for (int k = 0; k < 3; ++k) { h0[k] = scale_c(sc, h0[k]); h1[k] = scale_c(sc, h1[k]); }
+    } else if (flip) {
+      negate3(h0);
+      negate3(h1);
     }
     cplx<T> u[9];
     if constexpr (G == GStore::I16_12) load_link_q16<T>(U, geo.V, MU, n, u);
@@ -160,9 +171,7 @@ __global__ void __launch_bounds__(DslashBlock<T>::value, (EpiMinBlocks<T, Epi>::
     int c[4];
     site_coords(geo, s, c);
     cplx<T> acc[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = {(T)0, (T)0};
-    hop_dir<0, DAG, G, SI, T>(geo, U, in, s, c, acc);
+    hop_dir<0, DAG, G, SI, T, SingleIndex, true>(geo, U, in, s, c, acc);
     hop_dir<1, DAG, G, SI, T>(geo, U, in, s, c, acc);
     hop_dir<2, DAG, G, SI, T>(geo, U, in, s, c, acc);
     hop_dir<3, DAG, G, SI, T>(geo, U, in, s, c, acc);

@@ -108,7 +108,7 @@ struct lq_ctx {
   std::map<std::tuple<int, int, int, double>, lq::GraphEntry> graphs;
   void* batch = nullptr;                 // workspace of lq_solve_batch (k_batch.cu)
   int use_graphs = 1;                    // CG iterations as CUDA graphs (lq_set_option)
-  int df_updates = 0;                    // double-float intermediate reliable updates (lq_set_option)
+  int df_updates = 1;                    // double-float intermediate reliable updates (lq_set_option)
   int pair_sites = 0;                    // two-site packed stencil for 16-bit storage (lq_set_option)
   int staged = 0;                        // links shared in-block through shared memory (lq_set_option)
   int batch_rb = 0;                      // batched solves: right-hand sides per thread (0: autotuned)
@@ -176,6 +176,8 @@ void cg64_true_residual(lq_ctx* c, double kappa, int store_lo_prec, cudaStream_t
 // ---- double-float reliable update (k_cgdf.cu): x_df += x_lo; r = phi_df - M^dag M x_df
 // stored as r_df and in the inner format r_lo[prec]; |r|^2 -> state->rr_true
 void df_reliable_update(lq_ctx* c, double kappa, int inner_prec, cudaStream_t stream);
+// x_df += x_lo; x_lo = 0 (no residual)
+void df_accumulate(lq_ctx* c, int inner_prec, cudaStream_t stream);
 // x = 0, r = p = src in format s, from a double-float residual
 void launch_inner_restart_df(const Geom& g, SpinorRef src, SStore s, SpinorRef x, SpinorRef r, SpinorRef p,
                              cudaStream_t stream);
