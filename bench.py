@@ -854,7 +854,7 @@ def main():
     ap.add_argument("--kernel-only", default=None, choices=["dslash", "k1", "k2", "k3", "batch"],
                     help="profiling target: only launch this kernel (precision --prec); batch: a 12-RHS "
                          "batched solve of --steps iterations")
-    ap.add_argument("--prec", default="f32_12", choices=["f64", "f32", "f32_12", "f16_12", "bf16_12", "i16_12"])
+    ap.add_argument("--prec", default="f32_12", choices=["f64", "df64", "f32", "f32_12", "f16_12", "bf16_12", "i16_12"])
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
     ap.add_argument("--md-steps", type=int, default=25, help="leapfrog steps per trajectory (--hmc-ensemble)")
     ap.add_argument("--trajectories", type=int, default=20, help="--hmc-ensemble: number of trajectories")
