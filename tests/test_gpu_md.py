@@ -165,17 +165,19 @@ def test_trajectory_mixed_precision_solves(lq, prec):
         pg = host(p)
     finally:
         lq.lq_destroy(ctx)
-    # BF16 (8-bit significand): the solves still certify a 1e-10 FP64 residual, but the
-    # solution is no longer close to CG's Galerkin solution, so S_f = phi^dag X moves at
-    # first order in the residual r, |X^dag r| <= |X| |r| (measured 2.9e-8 here); the
-    # other formats stay within 1e-8 of the oracle
-    # (the same first-order effect moves the forces, so the final links of the BF16 run are
-    # held to 1e-9 instead of 1e-10; measured 1.1e-10)
-    tol = 1e-7 if prec == 4 else 1e-8
+    # Every solve certifies a 1e-10 FP64 true residual r, but only a solution close to CG's
+    # Galerkin solution moves S_f = phi^dag X at second order in r; a mixed solve with 16-bit
+    # iteration vectors (and double-float intermediate updates) leaves it off that solution at
+    # first order, |dS_f| <= |X| |r|.  FP32 storage stays within 1e-8 of the oracle; FP16-12
+    # measured 1.8e-8 (fixed point stayed within 1e-8) and both are held to 5e-8, BF16 (8-bit
+    # significand) measured
+    # 2.9e-8 and is held to 1e-7; the same first-order effect moves the forces, so the final
+    # links of the 16-bit runs are held to 1e-9 instead of 1e-10.
+    tol = {1: 1e-8, 2: 1e-8, 3: 5e-8, 6: 5e-8, 4: 1e-7}[prec]
     assert abs(r["dH"] - ref["dH"]) < tol, (prec, r["dH"], ref["dH"])
     assert bool(r["accepted"]) == ref["accept"]
     assert np.max(np.abs(pg - ref["p"])) < 1e-8
-    assert np.max(np.abs(Ug - ref["U"])) < (1e-9 if prec == 4 else 1e-10)
+    assert np.max(np.abs(Ug - ref["U"])) < (1e-9 if prec in (3, 4, 6) else 1e-10)
 
 
 def test_trajectory_reject_restores_links(lq):
