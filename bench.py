@@ -609,6 +609,7 @@ def run_kernel_only(args):
     U, phi = gauge_exp_iA(lat, SIGMA, SEED), source(lat, SEED)
     ctx = lq.lq_create(dims)
     lq.lq_set_option(ctx, lq.LQ_OPT_PAIR_SITES, args.pair_sites)
+    lq.lq_set_option(ctx, lq.LQ_OPT_STAGED, args.staged)
     lq.lq_gauge_set(ctx, torch.from_numpy(U).cuda())
     p = torch.from_numpy(phi).cuda()
     prec = lq.PRECISIONS[args.prec]
@@ -891,6 +892,8 @@ def main():
                     help="--hmc-ensemble: exp(iA) start (sigma 0.3, seed 8) or ordered start U = 1")
     ap.add_argument("--pair-sites", type=int, default=0, choices=[0, 1],
                     help="--kernel-only: two-site packed stencil for i16_12 (LQ_OPT_PAIR_SITES)")
+    ap.add_argument("--staged", type=int, default=0, choices=[0, 1],
+                    help="--kernel-only: the stencil sharing x and y links in-block (LQ_OPT_STAGED)")
     ap.add_argument("--hmc-ensemble", action="store_true",
                     help="run --steps HMC trajectories at 32^4 (beta 5.7, kappa 0.155, 25 steps) and report "
                          "acceptance and <exp(-dH)> instead of the benchmark")
