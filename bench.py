@@ -394,15 +394,18 @@ def measure_extras(lq, torch, dev):
             xs.append(torch.zeros_like(phs[-1]))
         res = {}
         try:
-            for pers in (0, 1):
+            # the whole solve as one graph with conditional nodes (default), one graph per
+            # chunk of iterations with the decisions on the host, one persistent launch per chunk
+            for form, pers, loop in (("device_loop", 0, 1), ("host_loop", 0, 0), ("persistent", 1, 0)):
                 lq.lq_set_option(ctxs[0], lq.LQ_OPT_BATCH_PERSISTENT, pers)
-                lq.lq_solve_batch(ctxs, xs, phs, kappas, R, 1e-10, 20000, prec, 50)       # tunes once
+                lq.lq_set_option(ctxs[0], lq.LQ_OPT_BATCH_DEVICE_LOOP, loop)
+                lq.lq_solve_batch(ctxs, xs, phs, kappas, R, 1e-10, 20000, prec, 50)       # tunes, records
                 torch.cuda.synchronize(dev)
                 t0 = time.perf_counter()
                 status, st, iters, resid, hist = lq.lq_solve_batch(ctxs, xs, phs, kappas, R, 1e-10, 20000, prec,
                                                                    50, hist_len=4000)
                 torch.cuda.synchronize(dev)
-                res["persistent" if pers else "graphs"] = {
+                res[form] = {
                     "seconds": time.perf_counter() - t0, "iterations": st["iterations"],
                     "reliable_updates": st["reliable_updates"], "kernel_launches": st["kernel_launches"],
                     "max_true_rel_resid": float(resid.max()), "column_iterations": [int(v) for v in iters]}
@@ -416,7 +419,7 @@ def measure_extras(lq, torch, dev):
                     lq.lq_solve_MdagM(cx, torch.zeros_like(rhs), rhs, k, 1e-10, 20000, prec, 50)
             torch.cuda.synchronize(dev)
             res["sequential_seconds"] = time.perf_counter() - t0
-            best = min(res["graphs"]["seconds"], res["persistent"]["seconds"])
+            best = min(res[f]["seconds"] for f in ("device_loop", "host_loop", "persistent"))
             res["speedup_vs_sequential"] = res["sequential_seconds"] / best
         finally:
             for cx in ctxs:
@@ -616,6 +619,9 @@ def run_kernel_only(args):
     if args.kernel_only == "batch":
         import numpy as np
         R = 12
+        # the profiled passes are the inner-format iterations; FP64 reliable updates keep the
+        # device footprint small (no double-float fields)
+        lq.lq_set_option(ctx, lq.LQ_OPT_DF64_UPDATES, 0)
         phis = torch.from_numpy(np.stack([source(lat, SEED, i) for i in range(R)])).cuda()
         x = torch.zeros_like(phis)
         t0 = time.perf_counter()
@@ -780,22 +786,27 @@ def run_ours(args):
         lq.lq_gauge_set(ctx, Uh)
         solve(inner, xh, phih)
         clocks_e2e = Clocks(local)
-        t_set, t_solve = [], []
+        t_set, t_solve, phases = [], [], []
         t_e = time.perf_counter()
         for _ in range(args.steps):
             ta = time.perf_counter()
             lq.lq_gauge_set(ctx, Uh)
             tb = time.perf_counter()
-            solve(inner, xh, phih)
+            st_e = solve(inner, xh, phih)
             t_set.append(tb - ta)
             t_solve.append(time.perf_counter() - tb)
+            phases.append((st_e["stage_ms"], st_e["solve_ms"], st_e["deliver_ms"]))
         e2e_local = time.perf_counter() - t_e
         clk_e2e = clocks_e2e.stop()
         e2e_t, e2e_units = replicas.combine(e2e_local, args.steps, dev)
         e2e = {"value": e2e_units / e2e_t, "unit": "solves/s", "h2d_bytes_per_step": int(U.nbytes + phi.nbytes),
                "d2h_bytes_per_step": int(phi.nbytes),
                "gauge_set_ms": round(1e3 * sorted(t_set)[len(t_set) // 2], 2),
-               "solve_ms": round(1e3 * sorted(t_solve)[len(t_solve) // 2], 2), "clocks": clk_e2e}
+               "solve_ms": round(1e3 * sorted(t_solve)[len(t_solve) // 2], 2), "clocks": clk_e2e,
+               # device time of the call's phases (CUDA events on its stream), median step
+               "call_phases_ms": dict(zip(("stage_in", "solve", "deliver"),
+                                          [round(sorted(p[i] for p in phases)[len(phases) // 2], 2)
+                                           for i in range(3)]))}
         # host <-> device copy rate of pinned buffers (context for e2e)
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         c0.record(stream)

@@ -91,6 +91,10 @@ typedef struct {
   double seconds;           /* host wall-clock of the call, from entry to the final synchronisation */
   int64_t kernel_launches;  /* kernels this call launched (every node of a CUDA graph counts once) */
   int escalations;          /* times the inner precision was raised to FP32 because it stagnated */
+  /* lq_solve_MdagM only (0 elsewhere): time on the context's stream (CUDA events) of staging
+   * the right-hand side (host-to-device copy and packing), of the solve, and of delivering
+   * the solution (unpacking and the device-to-host copy) */
+  double stage_ms, solve_ms, deliver_ms;
 } lq_solve_stats;
 
 /* Library version string. */
@@ -123,7 +127,10 @@ lq_status lq_set_stream(lq_ctx* ctx, void* cuda_stream);
  *                       triggered by the iterated residual meeting tol goes straight to the
  *                       FP64 certification); 0: every reliable update in FP64.  Same
  *                       iterations; on GB300 the double-float operator takes 1.5 ms against
- *                       3.3 ms for FP64 at 32^3 x 64.
+ *                       3.3 ms for FP64 at 32^3 x 64.  Batched solves (lq_solve_batch) read
+ *                       the option of their first context: double-float updates per column,
+ *                       FP64 certification once every column is frozen, which reopens a
+ *                       column whose FP64 residual misses tol.
  *   LQ_OPT_PAIR_SITES   0 (default): one site per thread; 1: with LQ_I16_12 and an even
  *                       L_t, the operator and the CG passes apply the stencil at two sites
  *                       per thread (x and x + L_t/2 in time) with packed FP32x2 arithmetic.
@@ -146,11 +153,20 @@ lq_status lq_set_stream(lq_ctx* ctx, void* cuda_stream);
  *                       device-wide barriers between the passes.  The barrier waits are
  *                       bounded (about one second); a wait that runs out makes the call
  *                       return LQ_ERR_TIMEOUT and leaves the context usable.
+ *   LQ_OPT_BATCH_DEVICE_LOOP  1 (default): without the persistent launch, lq_solve_batch runs
+ *                       the whole solve as one CUDA graph whose conditional nodes (a while
+ *                       loop over CG iterations inside a while loop over reliable updates,
+ *                       if nodes around the double-float residual and the FP64
+ *                       certification) take every convergence decision on the device; the
+ *                       host waits once.  Each loop stops at a cap taken from maxiter.
+ *                       0: the host launches a graph of reliable_every iterations, runs the
+ *                       reliable update and reads the state back once per chunk.
  *   LQ_OPT_BATCH_BARRIER_TEST  0 (default); 1: the persistent iteration's barrier also waits for
  *                       one block that does not exist, so every wait runs out: exercises the
  *                       LQ_ERR_TIMEOUT path (tests of the failure detection only). */
 enum { LQ_OPT_CUDA_GRAPHS = 1, LQ_OPT_DF64_UPDATES = 2, LQ_OPT_PAIR_SITES = 3, LQ_OPT_STAGED = 4,
-       LQ_OPT_BATCH_RHS_PER_THREAD = 5, LQ_OPT_BATCH_PERSISTENT = 6, LQ_OPT_BATCH_BARRIER_TEST = 7 };
+       LQ_OPT_BATCH_RHS_PER_THREAD = 5, LQ_OPT_BATCH_PERSISTENT = 6, LQ_OPT_BATCH_BARRIER_TEST = 7,
+       LQ_OPT_BATCH_DEVICE_LOOP = 8 };
 lq_status lq_set_option(lq_ctx* ctx, int option, int value);
 
 /* Number of lattice sites V. */
@@ -232,12 +248,14 @@ lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const double** phi, c
 
 /* The launch shape the autotuner of lq_solve_batch picked for the last batch shape solved
  * with ctx as ctxs[0]: threads per block (= sites per tile), right-hand sides per thread,
- * resident blocks per SM (0: all that fit); ms[0 .. ms_len) receives the measured time of
- * one iteration for every candidate in the order tried (rhs per thread 1, 2, 3, 4 among
- * the divisors of nrhs; for each, 256 threads with all blocks, 256 threads with one block
- * per SM, 128 threads).  Any output may be NULL.  Errors: LQ_ERR_STATE (no batched solve
- * yet). */
-lq_status lq_batch_tuning(lq_ctx* ctx, int* tile, int* rhs_per_thread, int* blocks_per_sm, double* ms, int ms_len);
+ * resident blocks per SM (0: all that fit), tile order (1: site-major, the right-hand-side
+ * groups of one site tile are consecutive tiles; 0: group-major); ms[0 .. ms_len) receives
+ * the measured time of one iteration for every candidate in the order tried (site-major
+ * first, then group-major; in each, rhs per thread 1, 2, 3, 4 among the divisors of nrhs;
+ * for each, 256 threads with all blocks, 256 threads with one block per SM, 128 threads).
+ * Any output may be NULL.  Errors: LQ_ERR_STATE (no batched solve yet). */
+lq_status lq_batch_tuning(lq_ctx* ctx, int* tile, int* rhs_per_thread, int* blocks_per_sm, int* site_major,
+                          double* ms, int ms_len);
 
 /* ---------------------------------------------------------------- MD */
 

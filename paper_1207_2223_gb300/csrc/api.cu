@@ -578,6 +578,7 @@ lq_status lq_create(lq_ctx** out, const int dims[4], int t_antiperiodic, void* c
   };
   chk(cudaGetDevice(&c->device), "cudaGetDevice");
   chk(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  for (cudaEvent_t& e : c->phase_ev) chk(cudaEventCreate(&e), "cudaEventCreate");
   const size_t spin = sizeof(double) * 24 * (size_t)V;
   chk(cudaMalloc(&c->gauge64, gauge_bytes(GStore::F64_18, (int)V)), "cudaMalloc gauge");
   chk(cudaMalloc(&c->stage_in, spin), "cudaMalloc stage");
@@ -605,6 +606,8 @@ lq_status lq_destroy(lq_ctx* c) {
   for (auto& kv : c->graphs)
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  for (cudaEvent_t e : c->phase_ev)
+    if (e) cudaEventDestroy(e);
   if (c->gauge64) cudaFree(c->gauge64);
   for (int p = 0; p < kNumPrec; ++p)
     if (c->gauge_lo[p]) cudaFree(c->gauge_lo[p]);
@@ -656,6 +659,7 @@ lq_status lq_set_option(lq_ctx* c, int option, int value) {
       if (c->batch) { destroy_batch_work(c->batch); c->batch = nullptr; }
       return LQ_OK;
     case LQ_OPT_BATCH_PERSISTENT: c->batch_persistent = value ? 1 : 0; return LQ_OK;
+    case LQ_OPT_BATCH_DEVICE_LOOP: c->batch_device_loop = value ? 1 : 0; return LQ_OK;
     case LQ_OPT_BATCH_BARRIER_TEST:
       if (value < 0 || value > 1) return fail(c, LQ_ERR_ARG, "barrier test option is 0 or 1");
       c->batch_barrier_extra = value;
@@ -755,16 +759,22 @@ lq_status lq_solve_MdagM(lq_ctx* c, double* x, const double* phi, double kappa, 
   double* hist_dev = nullptr;
   if (hist && hist_len > 0) LQ_CUDA(c, cudaMallocAsync((void**)&hist_dev, sizeof(double) * hist_len, c->stream));
   const double* dphi = nullptr;
+  cudaEventRecord(c->phase_ev[0], c->stream);
   LQ_TRY(stage_spinor_in(c, phi, &dphi));
   launch_pack_spinor(c->geo, dphi, SStore::F64, c->phi64.ref(), c->stream);
+  cudaEventRecord(c->phase_ev[1], c->stream);
   lq_solve_stats s{};
   lq_status result = solve_internal(c, kappa, tol, maxiter, inner, reliable_every, hist_dev, hist_len, &s);
+  cudaEventRecord(c->phase_ev[2], c->stream);
   s.kernel_launches += 1;
+  bool delivered = false;
   if (result == LQ_OK || result == LQ_ERR_NOT_CONVERGED) {
     lq_status d = deliver_spinor(c, c->x64, x);
     s.kernel_launches += 1;
     if (d != LQ_OK) result = d;
+    else delivered = true;
   }
+  cudaEventRecord(c->phase_ev[3], c->stream);
   if (hist_dev) {
     const int n = s.iterations < hist_len ? s.iterations : hist_len;
     if (n > 0) cudaMemcpyAsync(hist, hist_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
@@ -773,6 +783,15 @@ lq_status lq_solve_MdagM(lq_ctx* c, double* x, const double* phi, double kappa, 
   lq_status fin = cuda_check(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   if (result == LQ_OK) result = fin;
   s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  float ms[3] = {0.f, 0.f, 0.f};
+  for (int k = 0; k < 3; ++k)
+    if (cudaEventElapsedTime(&ms[k], c->phase_ev[k], c->phase_ev[k + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      ms[k] = 0.f;
+    }
+  s.stage_ms = ms[0];
+  s.solve_ms = ms[1];
+  s.deliver_ms = delivered ? ms[2] : 0.0;
   if (stats) *stats = s;
   return result;
 }

@@ -18,6 +18,7 @@ struct SysDesc {
   Geom geo;
   const void* gauge_lo;   // inner-format links of the system (SoA, stride V)
   const void* gauge64;    // FP64 links
+  const void* gauge_df;   // links as double-float pairs (double-float updates), else null
   double kappa;
   int R;                  // right-hand sides
   int off;                // first element in the batch fields
@@ -30,6 +31,7 @@ struct SysDesc {
 
 struct BatchDesc {
   int nsys, total, ncols, tile, ntiles, rb;
+  int site_major;         // tile order inside a system: 1 site tile outer, rhs group inner; 0 group outer
   SysDesc sys[kMaxSys];
 };
 
@@ -44,6 +46,12 @@ struct BatchState {
   int iter, iter_since_ru, ru_every, maxiter, halt, breakdown, hist_len;
   int timeout;             // a bounded wait of the persistent iteration gave up
   double* hist;            // [ncols][hist_len] relative iterated residuals
+  // device-side solve loop (one graph with conditional nodes): body counts of the
+  // current iteration loop and of the update loop (each loop stops at a cap), whether
+  // the current update skipped the double-float residual, and how many CG iterations,
+  // update cycles, double-float updates and FP64 certifications ran
+  int guard_inner, guard_outer, df_last;
+  int loops[4];
 };
 
 struct BatchReduce {
@@ -68,12 +76,21 @@ __device__ __forceinline__ int system_of_element(const BatchDesc& bd, int e) {
 struct TileWork {
   int k, r0, s;
 };
+template <bool ONE = false>
 __device__ __forceinline__ TileWork tile_work(const BatchDesc& bd, int t) {
-  const int k = system_of_tile(bd, t);
+  const int k = ONE ? 0 : system_of_tile(bd, t);
   const SysDesc& sd = bd.sys[k];
   const int rel = t - sd.tile0;
-  const int g = rel / sd.tpg;
-  return {k, g * bd.rb, (rel - g * sd.tpg) * bd.tile + (int)threadIdx.x};
+  int g, st;
+  if (bd.site_major) {            // the rhs groups of one site tile are consecutive tiles
+    const int ng = sd.R / bd.rb;
+    st = rel / ng;
+    g = rel - st * ng;
+  } else {                        // all site tiles of one rhs group, then the next group
+    g = rel / sd.tpg;
+    st = rel - g * sd.tpg;
+  }
+  return {k, g * bd.rb, st * bd.tile + (int)threadIdx.x};
 }
 
 // Column sums of one block (sh_col[ncols]) -> partials; the last block adds
@@ -204,6 +221,32 @@ struct BEpiCG2 {                             // r -= alpha M^dag t, x += alpha p
   }
 };
 
+// A column's true residual |r|^2 = tot after a reliable update: freeze the column once it
+// meets the tolerance (alpha = beta = 0 from then on), reopen a frozen column whose
+// residual no longer does (a double-float estimate that the FP64 certification overrules),
+// restart the search direction when the recursion drifted far from the true residual.
+__device__ __forceinline__ void reliable_update_column(BatchState* st, int c, double tot) {
+  st->rr_true[c] = tot;
+  if (!isfinite(tot)) { st->breakdown = 1; return; }
+  const bool meets = tot <= st->stop2 * st->phi2[c];
+  if (st->done[c] && meets) { st->beta[c] = 0.0; return; }
+  if (meets) {                                      // converged: freeze the column
+    st->done[c] = 1;
+    st->conv_iter[c] = st->iter;
+    st->beta[c] = 0.0;
+    st->alpha[c] = 0.0;
+  } else if (st->done[c] || tot > 100.0 * st->rr[c]) {
+    // reopened, or the low-precision recursion drifted far below the true
+    // residual: the search direction no longer fits it, restart from r
+    st->done[c] = 0;
+    st->beta[c] = 0.0;
+  } else {
+    st->beta[c] = tot / st->rr_prev[c];
+  }
+  st->rr[c] = tot;
+  st->rr_ref[c] = tot;
+}
+
 template <SStore S>
 struct BEpiResidual {                        // r64 = phi - M^dag tmp, r_lo = r64, rr_true = |r64|^2
   SpinorRef phi, r64, rlo;
@@ -225,25 +268,7 @@ struct BEpiResidual {                        // r64 = phi - M^dag tmp, r_lo = r6
     return a;
   }
   __device__ void finalize_cols(const double* tot, int ncols) const {
-    for (int c = 0; c < ncols; ++c) {
-      st->rr_true[c] = tot[c];
-      if (st->done[c]) { st->beta[c] = 0.0; continue; }
-      if (!isfinite(tot[c])) { st->breakdown = 1; continue; }
-      if (tot[c] <= st->stop2 * st->phi2[c]) {       // converged: freeze the column
-        st->done[c] = 1;
-        st->conv_iter[c] = st->iter;
-        st->beta[c] = 0.0;
-        st->alpha[c] = 0.0;
-      } else if (tot[c] > 100.0 * st->rr[c]) {
-        // the low-precision recursion drifted far below the true residual: the
-        // search direction no longer fits it, restart the column from r
-        st->beta[c] = 0.0;
-      } else {
-        st->beta[c] = tot[c] / st->rr_prev[c];
-      }
-      st->rr[c] = tot[c];
-      st->rr_ref[c] = tot[c];
-    }
+    for (int c = 0; c < ncols; ++c) reliable_update_column(st, c, tot[c]);
     st->iter_since_ru = 0;
     st->halt = 0;
   }
@@ -252,8 +277,9 @@ struct BEpiResidual {                        // r64 = phi - M^dag tmp, r_lo = r6
 // ------------------------------------------------------------ stencil
 // Both hops of direction MU at site s for RB right-hand sides: the links
 // U_mu(s) and U_mu(s - mu) are loaded and decoded once each and applied to the
-// RB neighbour spinors (column r0 + j at element e0 + j V + n).
-template <int MU, bool DAG, GStore G, SStore SI, typename T, int RB, int LD = 1>
+// RB neighbour spinors (column r0 + j at element e0 + j V + n).  INIT: the forward hop is
+// the site's first contribution and sets acc.
+template <int MU, bool DAG, GStore G, SStore SI, typename T, int RB, int LD = 1, bool INIT = false>
 __device__ __forceinline__ void batch_hops(const Geom& geo, int total, const GaugeRef& U, const SpinorRef& in, int s,
                                            const int c[4], int e0, cplx<T> (&acc)[RB][12]) {
   constexpr int SF = DAG ? +1 : -1;
@@ -279,7 +305,7 @@ __device__ __forceinline__ void batch_hops(const Geom& geo, int total, const Gau
       cplx<T> w0[3], w1[3];
       su3_mul(u, h0, w0);
       su3_mul(u, h1, w1);
-      accumulate<MU, SF>(acc[j], w0, w1);
+      accumulate<MU, SF, T, INIT>(acc[j], w0, w1);
     }
   }
   {
@@ -315,8 +341,10 @@ template <int RB> struct BatchMinBlocks<double, RB> { static constexpr int value
 
 // One stencil pass over the block's tiles: out = M in (or M^dag in) per right-hand side,
 // handed to the epilogue; with Epi::REDUCE the block's per-column sums are added to
-// sh_col (block-uniform calls: every thread of the block runs the same tiles).
-template <typename T, GStore G, SStore SI, bool DAG, int RB, class Epi, int LD = 1>
+// sh_col (block-uniform calls: every thread of the block runs the same tiles).  ONE: the
+// batch holds a single system, whose descriptor is then read at fixed offsets of the
+// kernel parameters (no per-access indexed constant loads).
+template <typename T, GStore G, SStore SI, bool DAG, int RB, class Epi, int LD = 1, bool ONE = false>
 __device__ __forceinline__ void batch_stencil_pass(const BatchDesc& bd, const SpinorRef& in, const Epi& epi,
                                                    int use64, double* sh_red, double* sh_col) {
   int cur = -1;                       // first column of the group the sums belong to
@@ -324,8 +352,8 @@ __device__ __forceinline__ void batch_stencil_pass(const BatchDesc& bd, const Sp
 #pragma unroll
   for (int j = 0; j < RB; ++j) red[j] = 0.0;
   for (int t = blockIdx.x; t < bd.ntiles; t += gridDim.x) {
-    const TileWork w = tile_work(bd, t);
-    const SysDesc& sd = bd.sys[w.k];
+    const TileWork w = tile_work<ONE>(bd, t);
+    const SysDesc& sd = bd.sys[ONE ? 0 : w.k];
     const int col0 = sd.col + w.r0;
     if constexpr (Epi::REDUCE) {
       if (col0 != cur) {            // block-uniform: every thread of the tile has the same columns
@@ -342,11 +370,7 @@ __device__ __forceinline__ void batch_stencil_pass(const BatchDesc& bd, const Sp
       const GaugeRef U{use64 ? sd.gauge64 : sd.gauge_lo};
       const int e0 = sd.off + w.r0 * sd.geo.V;
       cplx<T> acc[RB][12];
-#pragma unroll
-      for (int j = 0; j < RB; ++j)
-#pragma unroll
-        for (int q = 0; q < 12; ++q) acc[j][q] = {(T)0, (T)0};
-      batch_hops<0, DAG, G, SI, T, RB, LD>(sd.geo, bd.total, U, in, s, c, e0, acc);
+      batch_hops<0, DAG, G, SI, T, RB, LD, true>(sd.geo, bd.total, U, in, s, c, e0, acc);
       batch_hops<1, DAG, G, SI, T, RB, LD>(sd.geo, bd.total, U, in, s, c, e0, acc);
       batch_hops<2, DAG, G, SI, T, RB, LD>(sd.geo, bd.total, U, in, s, c, e0, acc);
       batch_hops<3, DAG, G, SI, T, RB, LD>(sd.geo, bd.total, U, in, s, c, e0, acc);
@@ -370,7 +394,7 @@ __device__ __forceinline__ void batch_stencil_pass(const BatchDesc& bd, const Sp
   }
 }
 
-template <typename T, GStore G, SStore SI, bool DAG, int RB, class Epi>
+template <typename T, GStore G, SStore SI, bool DAG, int RB, class Epi, bool ONE = false>
 __global__ void __launch_bounds__(256, (BatchMinBlocks<T, RB>::value))
     batch_dslash_kernel(BatchDesc bd, SpinorRef in, Epi epi, BatchReduce br, int use64) {
   if (epi.halted()) return;
@@ -378,7 +402,7 @@ __global__ void __launch_bounds__(256, (BatchMinBlocks<T, RB>::value))
   __shared__ double sh_red[RB * 32];
   for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) sh_col[c] = 0.0;
   __syncthreads();
-  batch_stencil_pass<T, G, SI, DAG, RB>(bd, in, epi, use64, sh_red, sh_col);
+  batch_stencil_pass<T, G, SI, DAG, RB, Epi, 1, ONE>(bd, in, epi, use64, sh_red, sh_col);
   if constexpr (Epi::REDUCE) {
     auto fin = [&](const double* tot) { epi.finalize_cols(tot, bd.ncols); };
     batch_grid_sum(bd, sh_col, br, fin);
@@ -624,10 +648,10 @@ struct BatchIterArgs {
   int per_sm;     // resident blocks per SM used by the stencil passes (0: all that fit)
 };
 
-template <typename T, GStore G, SStore SI, bool DAG, int RB, class Epi>
+template <typename T, GStore G, SStore SI, bool DAG, int RB, class Epi, bool ONE>
 void launch_batch_rb(const BatchDesc& bd, SpinorRef in, const Epi& epi, const BatchReduce& br, int use64, int sms,
                      int per_sm, cudaStream_t st) {
-  auto kern = &batch_dslash_kernel<T, G, SI, DAG, RB, Epi>;
+  auto kern = &batch_dslash_kernel<T, G, SI, DAG, RB, Epi, ONE>;
   static const int wave_all = resident_grid(reinterpret_cast<const void*>(kern), 256);
   // one wave of resident blocks (a second wave would sweep the lattice again and lose
   // the L2 reuse of neighbour spinors); per_sm > 0 caps the blocks per SM
@@ -641,13 +665,20 @@ template <typename T, GStore G, SStore SI, bool DAG, class Epi>
 void launch_batch(const BatchDesc& bd, SpinorRef in, const Epi& epi, const BatchReduce& br, int use64, int sms,
                   int per_sm, cudaStream_t st) {
   if constexpr (std::is_same<T, double>::value) {
-    launch_batch_rb<T, G, SI, DAG, 1>(bd, in, epi, br, use64, sms, per_sm, st);   // FP64: one per thread
+    launch_batch_rb<T, G, SI, DAG, 1, Epi, false>(bd, in, epi, br, use64, sms, per_sm, st);   // FP64: one per thread
+  } else if (bd.nsys == 1) {
+    switch (bd.rb) {
+      case 2: launch_batch_rb<T, G, SI, DAG, 2, Epi, true>(bd, in, epi, br, use64, sms, per_sm, st); break;
+      case 3: launch_batch_rb<T, G, SI, DAG, 3, Epi, true>(bd, in, epi, br, use64, sms, per_sm, st); break;
+      case 4: launch_batch_rb<T, G, SI, DAG, 4, Epi, true>(bd, in, epi, br, use64, sms, per_sm, st); break;
+      default: launch_batch_rb<T, G, SI, DAG, 1, Epi, true>(bd, in, epi, br, use64, sms, per_sm, st); break;
+    }
   } else {
     switch (bd.rb) {
-      case 2: launch_batch_rb<T, G, SI, DAG, 2>(bd, in, epi, br, use64, sms, per_sm, st); break;
-      case 3: launch_batch_rb<T, G, SI, DAG, 3>(bd, in, epi, br, use64, sms, per_sm, st); break;
-      case 4: launch_batch_rb<T, G, SI, DAG, 4>(bd, in, epi, br, use64, sms, per_sm, st); break;
-      default: launch_batch_rb<T, G, SI, DAG, 1>(bd, in, epi, br, use64, sms, per_sm, st); break;
+      case 2: launch_batch_rb<T, G, SI, DAG, 2, Epi, false>(bd, in, epi, br, use64, sms, per_sm, st); break;
+      case 3: launch_batch_rb<T, G, SI, DAG, 3, Epi, false>(bd, in, epi, br, use64, sms, per_sm, st); break;
+      case 4: launch_batch_rb<T, G, SI, DAG, 4, Epi, false>(bd, in, epi, br, use64, sms, per_sm, st); break;
+      default: launch_batch_rb<T, G, SI, DAG, 1, Epi, false>(bd, in, epi, br, use64, sms, per_sm, st); break;
     }
   }
 }
@@ -657,17 +688,37 @@ void launch_batch_xpay(const BatchDesc& bd, SStore s, SpinorRef r, SpinorRef p, 
                        int grid, cudaStream_t stream);
 
 // One CG iteration (t = M p; r -= alpha M^dag t, x += alpha p; p = r + beta p) of the batch
-// in the given storage, defined per format family in k_batch_f32.cu, k_batch_h16.cu, k_batch_i16.cu.
+// in the given storage, one translation unit per format (k_batch_f32.cu FP32-18,
+// k_batch_f32_12.cu, k_batch_h16.cu FP16-12, k_batch_bf16.cu, k_batch_i16.cu).
 void batch_iteration_f32(const BatchIterArgs& a, const BatchDesc& bd, int prec, cudaStream_t st);
+void batch_iteration_f32_12(const BatchIterArgs& a, const BatchDesc& bd, int prec, cudaStream_t st);
 void batch_iteration_h16(const BatchIterArgs& a, const BatchDesc& bd, int prec, cudaStream_t st);
+void batch_iteration_bf16(const BatchIterArgs& a, const BatchDesc& bd, int prec, cudaStream_t st);
 void batch_iteration_i16(const BatchIterArgs& a, const BatchDesc& bd, int prec, cudaStream_t st);
-// The persistent form of the same iterations (one cooperative launch), per format family.
+// The persistent form of the same iterations (one cooperative launch), per format.
 cudaError_t batch_persistent_f32(const BatchDesc& bd, const PersistArgs& a, int prec, int sms, int max_grid,
                                  cudaStream_t st);
+cudaError_t batch_persistent_f32_12(const BatchDesc& bd, const PersistArgs& a, int prec, int sms, int max_grid,
+                                    cudaStream_t st);
 cudaError_t batch_persistent_h16(const BatchDesc& bd, const PersistArgs& a, int prec, int sms, int max_grid,
                                  cudaStream_t st);
+cudaError_t batch_persistent_bf16(const BatchDesc& bd, const PersistArgs& a, int prec, int sms, int max_grid,
+                                  cudaStream_t st);
 cudaError_t batch_persistent_i16(const BatchDesc& bd, const PersistArgs& a, int prec, int sms, int max_grid,
                                  cudaStream_t st);
+
+// Double-float reliable update of the batch (k_batch_df.cu): x_df += x_lo, x_lo = 0
+// (`accumulate`) and per column r = phi - M^dag M x_df with r to r_lo and the column's
+// |r|^2 through reliable_update_column (`residual`).
+struct BatchDfArgs {
+  SpinorRef xlo, xdf, tmpdf, phidf, rlo;
+  BatchState* st;
+  BatchReduce br;
+  const void* gauge_df[kMaxSys];   // per system: links as double-float pairs
+  int flat_grid;
+  bool accumulate, residual;       // which of the two steps to launch
+};
+void batch_df_tail(const BatchDfArgs& a, const BatchDesc& bd, SStore s, cudaStream_t st);
 
 template <GStore G, SStore S>
 void batch_iteration_t(const BatchIterArgs& a, const BatchDesc& bd, cudaStream_t st) {

@@ -43,16 +43,16 @@ __device__ __forceinline__ cplx<df64> ldf(const float4* p, size_t i) {
 // and the spinor at the backward neighbour n.  flip: the hop crosses the antiperiodic
 // time boundary (sign -1).
 template <int MU, int S, bool FWD>
-__device__ __forceinline__ void df_hop(const float4* psi, const float4* U, int V, int n, int link_site, int half,
-                                       bool flip, cplx<df64> up[3], DFLower& lo) {
+__device__ __forceinline__ void df_hop(const float4* psi, const float4* U, int V, int sstride, int n, int link_site,
+                                       int half, bool flip, cplx<df64> up[3], DFLower& lo) {
   // spins of this lane: a (upper) and b (the partner in the projection)
   const int a = half;
   const int b = (MU <= 1) ? 3 - half : 2 + half;
   cplx<df64> h[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const cplx<df64> pa = ldf(psi, (size_t)(3 * a + c) * V + n);
-    const cplx<df64> pb = ldf(psi, (size_t)(3 * b + c) * V + n);
+    const cplx<df64> pa = ldf(psi, (size_t)(3 * a + c) * sstride + n);
+    const cplx<df64> pb = ldf(psi, (size_t)(3 * b + c) * sstride + n);
     // h0 (half 0) / h1 (half 1) of the projector (1 + S g_mu)
     cplx<df64> q;
     if constexpr (MU == 0) q = times_i(pb);                                     // x: p0 + S i p3, p1 + S i p2
@@ -94,25 +94,31 @@ __device__ __forceinline__ void df_hop(const float4* psi, const float4* U, int V
   }
 }
 
+// psi: the field shifted to the column's first element (site n at psi + chunk * sstride + n)
 template <int MU, bool DAG>
-__device__ __forceinline__ void df_dir(const Geom& geo, const float4* psi, const float4* U, int s, const int c[4],
-                                       int half, cplx<df64> up[3], DFLower& lo) {
+__device__ __forceinline__ void df_dir(const Geom& geo, const float4* psi, int sstride, const float4* U, int s,
+                                       const int c[4], int half, cplx<df64> up[3], DFLower& lo) {
   constexpr int SF = DAG ? +1 : -1;
   const int f = nbr_fwd(geo, s, c, MU);
-  df_hop<MU, SF, true>(psi, U, geo.V, f, s, half, MU == 3 && geo.antiperiodic && c[3] == geo.L[3] - 1, up, lo);
+  df_hop<MU, SF, true>(psi, U, geo.V, sstride, f, s, half, MU == 3 && geo.antiperiodic && c[3] == geo.L[3] - 1, up,
+                       lo);
   const int b = nbr_bwd(geo, s, c, MU);
-  df_hop<MU, -SF, false>(psi, U, geo.V, b, b, half, MU == 3 && geo.antiperiodic && c[3] == 0, up, lo);
+  df_hop<MU, -SF, false>(psi, U, geo.V, sstride, b, b, half, MU == 3 && geo.antiperiodic && c[3] == 0, up, lo);
 }
 
 __device__ __forceinline__ df64 shfl_df(df64 v) {
   return df64(__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1));
 }
 
-// out spins of lane `half`: v[0..2] = spin half, v[3..5] = spin half + 2 (colour fastest)
+// out spins of lane `half`: v[0..2] = spin half, v[3..5] = spin half + 2 (colour fastest).
+// Spinor fields are [chunk][element] with chunk stride `sstride` (V for a single lattice, the
+// batch's element count for one column of a batch) and the lattice's sites at elements
+// off .. off + V - 1; the epilogue gets the element index.
 template <bool DAG, class Epi>
 __global__ void __launch_bounds__(kDFSplitBlock, LQ_DFSPLIT_MIN_BLOCKS)
-    dslash_dfsplit_kernel(Geom geo, const float4* __restrict__ U, const float4* __restrict__ psi, df64 kappa,
-                          Epi epi, ReduceScratch rs) {
+    dslash_dfsplit_kernel(Geom geo, const float4* __restrict__ U, const float4* __restrict__ psi_base, int sstride,
+                          int off, df64 kappa, Epi epi, ReduceScratch rs) {
+  const float4* psi = psi_base + off;
   double red[1] = {0.0};
   const int half = threadIdx.x & 1;
   const int Vr = (geo.V + 15) & ~15;                     // whole warps iterate together
@@ -130,10 +136,10 @@ __global__ void __launch_bounds__(kDFSplitBlock, LQ_DFSPLIT_MIN_BLOCKS)
       lo.s2[i] = up[i];
       lo.s3[i] = up[i];
     }
-    df_dir<0, DAG>(geo, psi, U, ss, c, half, up, lo);
-    df_dir<1, DAG>(geo, psi, U, ss, c, half, up, lo);
-    df_dir<2, DAG>(geo, psi, U, ss, c, half, up, lo);
-    df_dir<3, DAG>(geo, psi, U, ss, c, half, up, lo);
+    df_dir<0, DAG>(geo, psi, sstride, U, ss, c, half, up, lo);
+    df_dir<1, DAG>(geo, psi, sstride, U, ss, c, half, up, lo);
+    df_dir<2, DAG>(geo, psi, sstride, U, ss, c, half, up, lo);
+    df_dir<3, DAG>(geo, psi, sstride, U, ss, c, half, up, lo);
     // lane 0 keeps spin 2 and hands its spin-3 sums to lane 1, and the other way round
     cplx<df64> v[6];
 #pragma unroll
@@ -148,10 +154,10 @@ __global__ void __launch_bounds__(kDFSplitBlock, LQ_DFSPLIT_MIN_BLOCKS)
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       const int comp = (k < 3) ? 3 * half + k : 3 * (half + 2) + (k - 3);
-      const cplx<df64> ctr = ldf(psi, (size_t)comp * geo.V + ss);
+      const cplx<df64> ctr = ldf(psi, (size_t)comp * sstride + ss);
       v[k] = {fma(-kappa, v[k].re, ctr.re), fma(-kappa, v[k].im, ctr.im)};
     }
-    epi.apply(geo.V, ss, half, active, v, red);
+    epi.apply(sstride, off + ss, half, active, v, red);
   }
   if constexpr (Epi::REDUCE) {
     double tot[1];
@@ -176,12 +182,19 @@ struct DFEpiStore {
   __device__ void finalize(double (&)[1]) const {}
 };
 
-// r = phi - M^dag tmp (double-float), r_lo = r in the inner format, rr_true = |r|^2
-template <SStore SLO>
+// |r|^2 of a single solve goes to its state
+struct DFFinSolver {
+  SolverState* st;
+  __device__ void operator()(double rr) const { st->rr_true = rr; }
+};
+
+// r = phi - M^dag tmp (double-float), r_lo = r in the inner format, |r|^2 to the
+// finaliser; RDF: r is also stored as a double-float field (rdf)
+template <SStore SLO, class Fin = DFFinSolver, bool RDF = true>
 struct DFEpiResidual {
   static constexpr bool REDUCE = true;
   SpinorRef phi, rdf, rlo;
-  SolverState* st;
+  Fin fin;
   __device__ void apply(int V, int s, int half, bool active, const cplx<df64> v[6], double (&red)[1]) const {
     const float4* ph = static_cast<const float4*>(phi.p);
     float4* rp = static_cast<float4*>(rdf.p);
@@ -192,7 +205,7 @@ struct DFEpiResidual {
       const int comp = (k < 3) ? 3 * half + k : 3 * (half + 2) + (k - 3);
       const cplx<df64> f = ldf(ph, (size_t)comp * V + s);
       const cplx<df64> r = {f.re - v[k].re, f.im - v[k].im};
-      if (active) rp[(size_t)comp * V + s] = make_float4(r.re.hi, r.re.lo, r.im.hi, r.im.lo);
+      if (RDF && active) rp[(size_t)comp * V + s] = make_float4(r.re.hi, r.re.lo, r.im.hi, r.im.lo);
       mine[k] = {(float)r.re, (float)r.im};
       a = fmaf(mine[k].re, mine[k].re, a);
       a = fmaf(mine[k].im, mine[k].im, a);
@@ -211,17 +224,19 @@ struct DFEpiResidual {
     if (active && half == 0) store_spinor<SLO, float>(rlo, V, s, full);
     if (active) red[0] += (double)a;
   }
-  __device__ void finalize(double (&tot)[1]) const { st->rr_true = tot[0]; }
+  __device__ void finalize(double (&tot)[1]) const { fin(tot[0]); }
 };
 
+// sstride < 0: a single lattice (chunk stride V, sites at elements 0 .. V - 1)
 template <bool DAG, class Epi>
 inline void launch_dslash_dfsplit(const Geom& geo, const void* U, SpinorRef in, double kappa, const Epi& epi,
-                                  const ReduceScratch& rs, cudaStream_t stream) {
+                                  const ReduceScratch& rs, cudaStream_t stream, int sstride = -1, int off = 0) {
   static const int wave =
       resident_grid(reinterpret_cast<const void*>(&dslash_dfsplit_kernel<DAG, Epi>), kDFSplitBlock);
   const int grid = std::max(1, std::min(grid_for(2 * geo.V, kDFSplitBlock), wave));
   dslash_dfsplit_kernel<DAG, Epi><<<grid, kDFSplitBlock, 0, stream>>>(
-      geo, static_cast<const float4*>(U), static_cast<const float4*>(in.p), df64(kappa), epi, rs);
+      geo, static_cast<const float4*>(U), static_cast<const float4*>(in.p), sstride < 0 ? geo.V : sstride, off,
+      df64(kappa), epi, rs);
 }
 
 }  // namespace lq

@@ -52,19 +52,11 @@ template <> __device__ __forceinline__ cplx<float> scale_c<float>(float s, cplx<
   return {r.x, r.y};
 }
 
-// Where the spinor of site n lives: one field of V sites (Single), or one
-// system of a batch whose right-hand sides are interleaved fastest inside a
-// field shared by all systems (Batched: element off + n R + r, chunk stride
-// = the batch's total number of elements).
+// Where the spinor of site n lives: element n of one field of V sites.
 struct SingleIndex {
   int V;
   __device__ __forceinline__ int stride() const { return V; }
   __device__ __forceinline__ int operator()(int n) const { return n; }
-};
-struct BatchIndex {
-  int total, off, R, r;
-  __device__ __forceinline__ int stride() const { return total; }
-  __device__ __forceinline__ int operator()(int n) const { return off + n * R + r; }
 };
 
 // Both hops of direction MU at site s.  INIT: the forward hop is the site's first

@@ -68,6 +68,7 @@ struct lq_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;         // work stream (the caller's)
   cudaStream_t capture_stream = nullptr; // private stream used only to record graphs
+  cudaEvent_t phase_ev[4] = {};          // phases of lq_solve_MdagM on the work stream
   std::string last_error;
 
   // gauge field: FP64 master copy and lazily built low-precision copies
@@ -114,6 +115,7 @@ struct lq_ctx {
   int batch_rb = 0;                      // batched solves: right-hand sides per thread (0: autotuned)
   int batch_persistent = 0;              // batched solves: one cooperative launch per chunk of iterations
   int batch_barrier_extra = 0;           // batched solves: phantom blocks the barrier waits for (timeout tests)
+  int batch_device_loop = 1;             // batched solves: the whole solve as one graph with conditional nodes
 };
 
 namespace lq {

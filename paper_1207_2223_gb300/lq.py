@@ -28,7 +28,8 @@ class LQError(RuntimeError):
 class lq_solve_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("converged", ctypes.c_int), ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64), ("escalations", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int64), ("escalations", ctypes.c_int), ("stage_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("deliver_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -91,7 +92,8 @@ SIGNATURES = {
     "lq_heatbath_draw": (_I, [_P, ctypes.c_uint64, ctypes.c_uint64, _P, _P, ctypes.POINTER(_D)]),
     "lq_philox4x32_10": (_I, [_P, _P, _P, _I]),
     "lq_time_fma_peak": (_I, [_P, _I, ctypes.POINTER(_D)]),
-    "lq_batch_tuning": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _P, _I]),
+    "lq_batch_tuning": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _P,
+                            _I]),
 }
 
 _lib = None
@@ -169,6 +171,7 @@ def lq_set_stream(ctx, stream):
 
 LQ_OPT_CUDA_GRAPHS, LQ_OPT_DF64_UPDATES, LQ_OPT_PAIR_SITES, LQ_OPT_STAGED = 1, 2, 3, 4
 LQ_OPT_BATCH_RHS_PER_THREAD, LQ_OPT_BATCH_PERSISTENT, LQ_OPT_BATCH_BARRIER_TEST = 5, 6, 7
+LQ_OPT_BATCH_DEVICE_LOOP = 8
 
 
 def lq_set_option(ctx, option, value):
@@ -246,12 +249,14 @@ def lq_solve_batch(ctxs, xs, phis, kappas, nrhs=1, tol=1e-10, maxiter=100000, in
 
 def lq_batch_tuning(ctx):
     """The autotuner's choice for the last batched solve on ctx: dict with tile (threads per
-    block), rhs_per_thread, blocks_per_sm (0: all that fit) and the per-candidate ms."""
+    block), rhs_per_thread, blocks_per_sm (0: all that fit), site_major (tile order) and the
+    per-candidate ms."""
     import numpy as np
-    t, rb, bps = _I(), _I(), _I()
-    ms = np.full(32, np.nan)
-    _check(ctx, load().lq_batch_tuning(ctx, ctypes.byref(t), ctypes.byref(rb), ctypes.byref(bps), ms.ctypes.data, 32))
-    return {"tile": t.value, "rhs_per_thread": rb.value, "blocks_per_sm": bps.value,
+    t, rb, bps, sm = _I(), _I(), _I(), _I()
+    ms = np.full(64, np.nan)
+    _check(ctx, load().lq_batch_tuning(ctx, ctypes.byref(t), ctypes.byref(rb), ctypes.byref(bps), ctypes.byref(sm),
+                                       ms.ctypes.data, 64))
+    return {"tile": t.value, "rhs_per_thread": rb.value, "blocks_per_sm": bps.value, "site_major": sm.value,
             "candidate_ms": [float(v) for v in ms if v == v]}
 
 

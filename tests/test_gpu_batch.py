@@ -179,7 +179,7 @@ def test_rhs_per_thread_variants_match_oracle(lq, rb, prec):
     finally:
         lq.lq_destroy(ctx)
     assert status == lq.LQ_OK and np.all(resid <= 1e-10)
-    assert tune["rhs_per_thread"] == rb and tune["tile"] == 256
+    assert tune["rhs_per_thread"] == rb and tune["tile"] == 256 and tune["site_major"] == 1
     for i in (0, 7, 11):
         xr, _, _ = cg_MdagM(U, phis[i], dims, kappa, 1e-13)
         assert rel_err(xs[i], xr) < X_TOL
@@ -210,8 +210,8 @@ def test_autotuner_reports_its_choice(lq):
         lq.lq_destroy(ctx)
     assert s1[0] == s2[0] == lq.LQ_OK
     assert torch.equal(x, x2)
-    # rhs per thread 1, 2, 3 divide 6 (4 does not): 3 shapes each
-    assert len(t1["candidate_ms"]) == 9 and t1["rhs_per_thread"] in (1, 2, 3)
+    # two tile orders x rhs per thread 1, 2, 3 (divisors of 6) x 3 shapes
+    assert len(t1["candidate_ms"]) == 18 and t1["rhs_per_thread"] in (1, 2, 3) and t1["site_major"] in (0, 1)
     assert min(t1["candidate_ms"]) > 0 and t1 == t2
 
 
@@ -295,3 +295,96 @@ def test_persistent_barrier_timeout_is_reported_and_recoverable(lq):
         assert status == lq.LQ_OK
     finally:
         lq.lq_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [2, 3, 6])
+def test_double_float_updates_match_fp64_updates(lq, prec):
+    """The batch's intermediate reliable updates in double-float arithmetic (the default) and
+    in FP64 throughout give solutions that agree within the conditioning bound and with the
+    oracle; both end on an FP64-certified residual, for right-hand sides sharing links and for
+    uneven lattices, and a tolerance of 1e-12 is still met (certified in FP64)."""
+    shapes = [(4, 4, 4, 8), (2, 4, 6, 4), (6, 2, 2, 4)]
+    kappas = [0.15, 0.14, 0.155]
+    R = 3
+    Us = [gauge_exp_iA(Lattice(d), 0.3, 30 + k) for k, d in enumerate(shapes)]
+    phis = [np.stack([source(Lattice(d), 30 + k, i) for i in range(R)]) for k, d in enumerate(shapes)]
+    sols, stats = {}, {}
+    for df in (1, 0):
+        ctxs, xs = [], []
+        try:
+            for k, d in enumerate(shapes):
+                c = lq.lq_create(d)
+                lq.lq_gauge_set(c, dev(Us[k]))
+                ctxs.append(c)
+                xs.append(torch.zeros_like(dev(phis[k])))
+            lq.lq_set_option(ctxs[0], lq.LQ_OPT_DF64_UPDATES, df)
+            status, st, iters, resid, _ = lq.lq_solve_batch(ctxs, xs, [dev(p) for p in phis], kappas, R, 1e-10,
+                                                            5000, prec, 25)
+            assert status == lq.LQ_OK and np.all(resid <= 1e-10), (df, resid)
+            sols[df] = [host(x) for x in xs]
+            stats[df] = st
+            for k in range(len(shapes)):
+                res = _true_residuals(lq, shapes[k], dev(Us[k]), [xs[k][i] for i in range(R)],
+                                      [dev(phis[k][i]) for i in range(R)], kappas[k])
+                assert max(res) <= 1e-10, (df, k, res)
+            if df:
+                xt = [torch.zeros_like(x) for x in xs]
+                status, st, iters, resid, _ = lq.lq_solve_batch(ctxs, xt, [dev(p) for p in phis], kappas, R,
+                                                                1e-12, 5000, lq.LQ_F32, 25)
+                assert status == lq.LQ_OK and np.all(resid <= 1e-12), resid
+                res = _true_residuals(lq, shapes[0], dev(Us[0]), [xt[0][i] for i in range(R)],
+                                      [dev(phis[0][i]) for i in range(R)], kappas[0])
+                assert max(res) <= 1e-12, res
+        finally:
+            for c in ctxs:
+                lq.lq_destroy(c)
+    for k in range(len(shapes)):
+        assert rel_err(sols[1][k], sols[0][k]) < X_TOL, k
+        xr, _, _ = cg_MdagM(Us[k], phis[k][1], shapes[k], kappas[k], 1e-13)
+        assert rel_err(sols[1][k][1], xr) < X_TOL, k
+    assert stats[1]["kernel_launches"] > 0 and stats[0]["kernel_launches"] > 0
+
+
+@pytest.mark.parametrize("df", [1, 0])
+def test_device_loop_matches_host_loop(lq, df):
+    """The whole solve as one graph whose conditional nodes take every convergence decision on
+    the device (the default) and the host loop (one graph per chunk of iterations, decisions on
+    the host) run the same kernels in the same order: bit-identical solutions, histories,
+    iteration and reliable-update counts, with double-float or FP64 intermediate updates, for
+    right-hand sides sharing links and uneven lattices.  An unreachable tolerance ends at the
+    iteration limit with LQ_ERR_NOT_CONVERGED."""
+    shapes = [(4, 4, 4, 8), (2, 4, 6, 4)]
+    kappas = [0.15, 0.155]
+    R = 2
+    Us = [gauge_exp_iA(Lattice(d), 0.3, 40 + k) for k, d in enumerate(shapes)]
+    phis = [np.stack([source(Lattice(d), 40 + k, i) for i in range(R)]) for k, d in enumerate(shapes)]
+    out = {}
+    for loop in (1, 0):
+        ctxs = []
+        try:
+            for k, d in enumerate(shapes):
+                c = lq.lq_create(d)
+                lq.lq_gauge_set(c, dev(Us[k]))
+                ctxs.append(c)
+            lq.lq_set_option(ctxs[0], lq.LQ_OPT_DF64_UPDATES, df)
+            lq.lq_set_option(ctxs[0], lq.LQ_OPT_BATCH_DEVICE_LOOP, loop)
+            xs = [torch.zeros_like(dev(p)) for p in phis]
+            status, st, iters, resid, hist = lq.lq_solve_batch(ctxs, xs, [dev(p) for p in phis], kappas, R, 1e-10,
+                                                               5000, lq.LQ_F16_12, 25, hist_len=2000)
+            assert status == lq.LQ_OK and np.all(resid <= 1e-10), (loop, resid)
+            out[loop] = ([host(x) for x in xs], st, iters, resid, hist)
+            xt = [torch.zeros_like(dev(p)) for p in phis]
+            status, st2, _, _, _ = lq.lq_solve_batch(ctxs, xt, [dev(p) for p in phis], kappas, R, 1e-30, 30,
+                                                     lq.LQ_F16_12, 25)
+            assert status == lq.LQ_ERR_NOT_CONVERGED and st2["iterations"] == 30, (loop, st2)
+        finally:
+            for c in ctxs:
+                lq.lq_destroy(c)
+    (x1, s1, i1, r1, h1), (x0, s0, i0, r0, h0) = out[1], out[0]
+    for a, b in zip(x1, x0):
+        assert np.array_equal(a, b)
+    assert np.array_equal(i1, i0) and np.array_equal(r1, r0) and np.array_equal(h1, h0)
+    assert s1["iterations"] == s0["iterations"] and s1["reliable_updates"] == s0["reliable_updates"]
+    assert s1["converged"] == s0["converged"] == 1
+    xr, _, _ = cg_MdagM(Us[1], phis[1][0], shapes[1], kappas[1], 1e-13)
+    assert rel_err(x1[1][0], xr) < X_TOL
