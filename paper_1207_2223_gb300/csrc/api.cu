@@ -45,6 +45,19 @@ bool is_device_ptr(const void* p) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// With LQ_OPT_HOST_DIRECT: the device address of a page-locked host buffer mapped into the
+// device's address space (kernels then read or write it directly, no staging copy); null
+// for device buffers, pageable host memory, or with the option off.
+void* host_direct(const lq_ctx* c, const void* p) {
+  if (!c->host_direct) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 lq_status alloc_field(lq_ctx* c, Field& f, SStore s) {
   if (f.data) return LQ_OK;
   f.store = s;
@@ -88,6 +101,7 @@ lq_status stage_spinor_in(lq_ctx* c, const double* in, const double** dev) {
   if (!in) return fail(c, LQ_ERR_ARG, "null spinor buffer");
   if (!aligned16(in)) return fail(c, LQ_ERR_ARG, "spinor buffer not 16-byte aligned");
   if (is_device_ptr(in)) { *dev = in; return LQ_OK; }
+  if (const void* d = host_direct(c, in)) { *dev = static_cast<const double*>(d); return LQ_OK; }
   LQ_CUDA(c, cudaMemcpyAsync(c->stage_in, in, sizeof(double) * 24 * c->geo.V, cudaMemcpyHostToDevice, c->stream));
   *dev = c->stage_in;
   return LQ_OK;
@@ -100,6 +114,12 @@ lq_status deliver_spinor(lq_ctx* c, const Field& f, double* out) {
   if (is_device_ptr(out)) {
     launch_unpack_spinor(c->geo, f.store, f.ref(), out, c->stream);
     LQ_CUDA(c, cudaGetLastError());
+    return LQ_OK;
+  }
+  if (void* d = host_direct(c, out)) {
+    launch_unpack_spinor(c->geo, f.store, f.ref(), static_cast<double*>(d), c->stream);
+    LQ_CUDA(c, cudaGetLastError());
+    LQ_CUDA(c, cudaStreamSynchronize(c->stream));
     return LQ_OK;
   }
   launch_unpack_spinor(c->geo, f.store, f.ref(), c->stage_out, c->stream);
@@ -660,6 +680,7 @@ lq_status lq_set_option(lq_ctx* c, int option, int value) {
       return LQ_OK;
     case LQ_OPT_BATCH_PERSISTENT: c->batch_persistent = value ? 1 : 0; return LQ_OK;
     case LQ_OPT_BATCH_DEVICE_LOOP: c->batch_device_loop = value ? 1 : 0; return LQ_OK;
+    case LQ_OPT_HOST_DIRECT: c->host_direct = value ? 1 : 0; return LQ_OK;
     case LQ_OPT_BATCH_BARRIER_TEST:
       if (value < 0 || value > 1) return fail(c, LQ_ERR_ARG, "barrier test option is 0 or 1");
       c->batch_barrier_extra = value;
@@ -673,7 +694,9 @@ lq_status lq_gauge_set(lq_ctx* c, const double* U) {
   if (!U) return fail(c, LQ_ERR_ARG, "null gauge buffer");
   if (!aligned16(U)) return fail(c, LQ_ERR_ARG, "gauge buffer not 16-byte aligned");
   const double* src = U;
-  if (!is_device_ptr(U)) {
+  if (const void* d = is_device_ptr(U) ? nullptr : host_direct(c, U)) {
+    src = static_cast<const double*>(d);                    // read in place by the packing kernel
+  } else if (!is_device_ptr(U)) {
     if (!c->stage_gauge) LQ_CUDA(c, cudaMalloc(&c->stage_gauge, sizeof(double) * 72 * (size_t)c->geo.V));
     LQ_CUDA(c, cudaMemcpyAsync(c->stage_gauge, U, sizeof(double) * 72 * (size_t)c->geo.V, cudaMemcpyHostToDevice,
                                c->stream));
@@ -683,7 +706,7 @@ lq_status lq_gauge_set(lq_ctx* c, const double* U) {
   LQ_CUDA(c, cudaGetLastError());
   for (int p = 0; p < kNumPrec; ++p) c->gauge_lo_valid[p] = false;
   c->gauge_set = true;
-  if (src != U) LQ_CUDA(c, cudaStreamSynchronize(c->stream));   // the host buffer may be reused at once
+  if (!is_device_ptr(U)) LQ_CUDA(c, cudaStreamSynchronize(c->stream));   // the host buffer may be reused at once
   return LQ_OK;
 }
 
@@ -695,6 +718,12 @@ lq_status lq_gauge_get(lq_ctx* c, double* U) {
   if (is_device_ptr(U)) {
     launch_unpack_gauge64(c->geo, c->gauge64, U, c->stream);
     LQ_CUDA(c, cudaGetLastError());
+    return LQ_OK;
+  }
+  if (void* d = host_direct(c, U)) {
+    launch_unpack_gauge64(c->geo, c->gauge64, static_cast<double*>(d), c->stream);
+    LQ_CUDA(c, cudaGetLastError());
+    LQ_CUDA(c, cudaStreamSynchronize(c->stream));
     return LQ_OK;
   }
   if (!c->stage_gauge) LQ_CUDA(c, cudaMalloc(&c->stage_gauge, sizeof(double) * 72 * (size_t)c->geo.V));

@@ -31,24 +31,44 @@ size_t gauge_bytes(GStore g, int V) {
   }
 }
 
-__global__ void pack_gauge64_kernel(int V, const double* __restrict__ canon, double2* __restrict__ soa) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= V) return;
-  const double2* src = reinterpret_cast<const double2*>(canon) + (size_t)s * 36;
-#pragma unroll
-  for (int mu = 0; mu < 4; ++mu)
-#pragma unroll
-    for (int c = 0; c < 9; ++c) soa[((size_t)mu * 9 + c) * V + s] = src[mu * 9 + c];
+// The canonical layouts are read and written in contiguous runs: a block stages the
+// canonical records of a tile of sites in shared memory (row padded by one complex entry)
+// and the structure-of-arrays side is accessed one component at a time across the tile.
+// Coalesced on both sides, which matters most when the canonical buffer is host memory
+// accessed in place.
+constexpr int kGaugeTile = 64;           // sites per block, 36 complex entries each
+constexpr int kSpinTile = 128;           // sites per block, 12 complex entries each
+
+__global__ void __launch_bounds__(256) pack_gauge64_kernel(int V, const double2* __restrict__ canon,
+                                                           double2* __restrict__ soa) {
+  __shared__ double2 sh[kGaugeTile * 37];
+  const int s0 = blockIdx.x * kGaugeTile;
+  const int n = min(kGaugeTile, V - s0);
+  for (int i = threadIdx.x; i < n * 36; i += blockDim.x) {
+    const int sl = i / 36;
+    sh[sl * 37 + (i - sl * 36)] = canon[(size_t)s0 * 36 + i];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n * 36; i += blockDim.x) {
+    const int k = i / n, sl = i - k * n;
+    soa[(size_t)k * V + s0 + sl] = sh[sl * 37 + k];
+  }
 }
 
-__global__ void unpack_gauge64_kernel(int V, const double2* __restrict__ soa, double* __restrict__ canon) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= V) return;
-  double2* dst = reinterpret_cast<double2*>(canon) + (size_t)s * 36;
-#pragma unroll
-  for (int mu = 0; mu < 4; ++mu)
-#pragma unroll
-    for (int c = 0; c < 9; ++c) dst[mu * 9 + c] = soa[((size_t)mu * 9 + c) * V + s];
+__global__ void __launch_bounds__(256) unpack_gauge64_kernel(int V, const double2* __restrict__ soa,
+                                                             double2* __restrict__ canon) {
+  __shared__ double2 sh[kGaugeTile * 37];
+  const int s0 = blockIdx.x * kGaugeTile;
+  const int n = min(kGaugeTile, V - s0);
+  for (int i = threadIdx.x; i < n * 36; i += blockDim.x) {
+    const int k = i / n, sl = i - k * n;
+    sh[sl * 37 + k] = soa[(size_t)k * V + s0 + sl];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n * 36; i += blockDim.x) {
+    const int sl = i / 36;
+    canon[(size_t)s0 * 36 + i] = sh[sl * 37 + (i - sl * 36)];
+  }
 }
 
 template <GStore G>
@@ -99,34 +119,52 @@ __global__ void convert_gauge_kernel(int V, const double2* __restrict__ soa64, v
 }
 
 template <SStore S>
-__global__ void pack_spinor_kernel(int V, const double* __restrict__ canon, SpinorRef out) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= V) return;
-  const double2* src = reinterpret_cast<const double2*>(canon) + (size_t)s * 12;
+__global__ void __launch_bounds__(kSpinTile) pack_spinor_kernel(int V, const double2* __restrict__ canon,
+                                                                SpinorRef out) {
+  __shared__ double2 sh[kSpinTile * 13];
+  const int s0 = blockIdx.x * kSpinTile;
+  const int n = min(kSpinTile, V - s0);
+  for (int i = threadIdx.x; i < n * 12; i += blockDim.x) {
+    const int sl = i / 12;
+    sh[sl * 13 + (i - sl * 12)] = canon[(size_t)s0 * 12 + i];
+  }
+  __syncthreads();
+  const int sl = threadIdx.x;
+  if (sl >= n) return;
   cplx<double> v[12];
 #pragma unroll
-  for (int c = 0; c < 12; ++c) { double2 w = src[c]; v[c] = {w.x, w.y}; }
-  store_spinor<S, double>(out, V, s, v);
+  for (int c = 0; c < 12; ++c) { const double2 w = sh[sl * 13 + c]; v[c] = {w.x, w.y}; }
+  store_spinor<S, double>(out, V, s0 + sl, v);
 }
 
 template <SStore S>
-__global__ void unpack_spinor_kernel(int V, SpinorRef in, double* __restrict__ canon) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= V) return;
-  cplx<double> v[12];
-  load_spinor<S, double>(in, V, s, v);
-  double2* dst = reinterpret_cast<double2*>(canon) + (size_t)s * 12;
+__global__ void __launch_bounds__(kSpinTile) unpack_spinor_kernel(int V, SpinorRef in, double2* __restrict__ canon) {
+  __shared__ double2 sh[kSpinTile * 13];
+  const int s0 = blockIdx.x * kSpinTile;
+  const int n = min(kSpinTile, V - s0);
+  const int sl = threadIdx.x;
+  if (sl < n) {
+    cplx<double> v[12];
+    load_spinor<S, double>(in, V, s0 + sl, v);
 #pragma unroll
-  for (int c = 0; c < 12; ++c) dst[c] = make_double2(v[c].re, v[c].im);
+    for (int c = 0; c < 12; ++c) sh[sl * 13 + c] = make_double2(v[c].re, v[c].im);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n * 12; i += blockDim.x) {
+    const int t = i / 12;
+    canon[(size_t)s0 * 12 + i] = sh[t * 13 + (i - t * 12)];
+  }
 }
 
 static constexpr int kBS = 256;
 
 void launch_pack_gauge64(const Geom& g, const double* canon, void* soa, cudaStream_t st) {
-  pack_gauge64_kernel<<<grid_for(g.V, kBS), kBS, 0, st>>>(g.V, canon, static_cast<double2*>(soa));
+  pack_gauge64_kernel<<<grid_for(g.V, kGaugeTile), 256, 0, st>>>(g.V, reinterpret_cast<const double2*>(canon),
+                                                                  static_cast<double2*>(soa));
 }
 void launch_unpack_gauge64(const Geom& g, const void* soa, double* canon, cudaStream_t st) {
-  unpack_gauge64_kernel<<<grid_for(g.V, kBS), kBS, 0, st>>>(g.V, static_cast<const double2*>(soa), canon);
+  unpack_gauge64_kernel<<<grid_for(g.V, kGaugeTile), 256, 0, st>>>(g.V, static_cast<const double2*>(soa),
+                                                                    reinterpret_cast<double2*>(canon));
 }
 void launch_convert_gauge(const Geom& g, const void* soa64, GStore dst, void* out, cudaStream_t st) {
   const double2* in = static_cast<const double2*>(soa64);
@@ -160,25 +198,27 @@ void launch_convert_spinor(const Geom& g, SStore a, SpinorRef in, SStore b, Spin
     convert_spinor_kernel<SStore::DF64, SStore::F64><<<grid, kBS, 0, st>>>(g.V, in, out);
 }
 void launch_pack_spinor(const Geom& g, const double* canon, SStore s, SpinorRef out, cudaStream_t st) {
-  const int grid = grid_for(g.V, kBS);
+  const int grid = grid_for(g.V, kSpinTile);
+  const double2* in = reinterpret_cast<const double2*>(canon);
   switch (s) {
-    case SStore::F64: pack_spinor_kernel<SStore::F64><<<grid, kBS, 0, st>>>(g.V, canon, out); break;
-    case SStore::F32: pack_spinor_kernel<SStore::F32><<<grid, kBS, 0, st>>>(g.V, canon, out); break;
-    case SStore::F16: pack_spinor_kernel<SStore::F16><<<grid, kBS, 0, st>>>(g.V, canon, out); break;
-    case SStore::BF16: pack_spinor_kernel<SStore::BF16><<<grid, kBS, 0, st>>>(g.V, canon, out); break;
-    case SStore::DF64: pack_spinor_kernel<SStore::DF64><<<grid, kBS, 0, st>>>(g.V, canon, out); break;
-    case SStore::I16: pack_spinor_kernel<SStore::I16><<<grid, kBS, 0, st>>>(g.V, canon, out); break;
+    case SStore::F64: pack_spinor_kernel<SStore::F64><<<grid, kSpinTile, 0, st>>>(g.V, in, out); break;
+    case SStore::F32: pack_spinor_kernel<SStore::F32><<<grid, kSpinTile, 0, st>>>(g.V, in, out); break;
+    case SStore::F16: pack_spinor_kernel<SStore::F16><<<grid, kSpinTile, 0, st>>>(g.V, in, out); break;
+    case SStore::BF16: pack_spinor_kernel<SStore::BF16><<<grid, kSpinTile, 0, st>>>(g.V, in, out); break;
+    case SStore::DF64: pack_spinor_kernel<SStore::DF64><<<grid, kSpinTile, 0, st>>>(g.V, in, out); break;
+    case SStore::I16: pack_spinor_kernel<SStore::I16><<<grid, kSpinTile, 0, st>>>(g.V, in, out); break;
   }
 }
 void launch_unpack_spinor(const Geom& g, SStore s, SpinorRef in, double* canon, cudaStream_t st) {
-  const int grid = grid_for(g.V, kBS);
+  const int grid = grid_for(g.V, kSpinTile);
+  double2* out = reinterpret_cast<double2*>(canon);
   switch (s) {
-    case SStore::F64: unpack_spinor_kernel<SStore::F64><<<grid, kBS, 0, st>>>(g.V, in, canon); break;
-    case SStore::F32: unpack_spinor_kernel<SStore::F32><<<grid, kBS, 0, st>>>(g.V, in, canon); break;
-    case SStore::F16: unpack_spinor_kernel<SStore::F16><<<grid, kBS, 0, st>>>(g.V, in, canon); break;
-    case SStore::BF16: unpack_spinor_kernel<SStore::BF16><<<grid, kBS, 0, st>>>(g.V, in, canon); break;
-    case SStore::DF64: unpack_spinor_kernel<SStore::DF64><<<grid, kBS, 0, st>>>(g.V, in, canon); break;
-    case SStore::I16: unpack_spinor_kernel<SStore::I16><<<grid, kBS, 0, st>>>(g.V, in, canon); break;
+    case SStore::F64: unpack_spinor_kernel<SStore::F64><<<grid, kSpinTile, 0, st>>>(g.V, in, out); break;
+    case SStore::F32: unpack_spinor_kernel<SStore::F32><<<grid, kSpinTile, 0, st>>>(g.V, in, out); break;
+    case SStore::F16: unpack_spinor_kernel<SStore::F16><<<grid, kSpinTile, 0, st>>>(g.V, in, out); break;
+    case SStore::BF16: unpack_spinor_kernel<SStore::BF16><<<grid, kSpinTile, 0, st>>>(g.V, in, out); break;
+    case SStore::DF64: unpack_spinor_kernel<SStore::DF64><<<grid, kSpinTile, 0, st>>>(g.V, in, out); break;
+    case SStore::I16: unpack_spinor_kernel<SStore::I16><<<grid, kSpinTile, 0, st>>>(g.V, in, out); break;
   }
 }
 

@@ -12,6 +12,7 @@ namespace lq {
 
 constexpr int kMaxSys = 16;
 constexpr int kMaxCols = 64;
+constexpr int kMaxWarps = 8;          // warps per block of the batched passes (<= 256 threads)
 constexpr int kMaxRB = 4;
 
 struct SysDesc {
@@ -129,6 +130,39 @@ __device__ __forceinline__ void flush_columns(double (&v)[RB], int col0, double*
 #pragma unroll
     for (int q = 0; q < RB; ++q) sh_col[col0 + q] += v[q];
   }
+  __syncthreads();
+}
+
+// Adds the warp's per-thread sums v[0..RB) to its slots of columns col0 .. col0 + RB - 1
+// (sh_wcol[column * kMaxWarps + warp]): a fixed butterfly over the lanes, no block-wide
+// synchronisation (warp-uniform call).
+template <int RB>
+__device__ __forceinline__ void flush_columns_warp(double (&v)[RB], int col0, double* sh_wcol) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < RB; ++q) {
+    double x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sh_wcol[(col0 + q) * kMaxWarps + warp] += x;
+  }
+}
+
+// sh_col[c] = the warps' slots of column c added in warp order (block-wide, synchronises).
+__device__ __forceinline__ void gather_columns(int ncols, const double* sh_wcol, double* sh_col) {
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+    double a = 0.0;
+    for (int w = 0; w < nw; ++w) a += sh_wcol[c * kMaxWarps + w];
+    sh_col[c] = a;
+  }
+  __syncthreads();
+}
+
+// Zeroes the warp slots of every column (block-wide, synchronises).
+__device__ __forceinline__ void clear_columns(int ncols, double* sh_wcol) {
+  for (int i = threadIdx.x; i < ncols * kMaxWarps; i += blockDim.x) sh_wcol[i] = 0.0;
   __syncthreads();
 }
 
@@ -340,13 +374,15 @@ template <typename T, int RB> struct BatchMinBlocks { static constexpr int value
 template <int RB> struct BatchMinBlocks<double, RB> { static constexpr int value = 1; };
 
 // One stencil pass over the block's tiles: out = M in (or M^dag in) per right-hand side,
-// handed to the epilogue; with Epi::REDUCE the block's per-column sums are added to
-// sh_col (block-uniform calls: every thread of the block runs the same tiles).  ONE: the
+// handed to the epilogue; with Epi::REDUCE every warp adds its per-column sums to its slots
+// of sh_wcol (cleared by the caller) whenever the block moves to another rhs group, and
+// the pass ends with the block's column sums in sh_col (block-uniform calls: every thread
+// of the block runs the same tiles).  ONE: the
 // batch holds a single system, whose descriptor is then read at fixed offsets of the
 // kernel parameters (no per-access indexed constant loads).
 template <typename T, GStore G, SStore SI, bool DAG, int RB, class Epi, int LD = 1, bool ONE = false>
 __device__ __forceinline__ void batch_stencil_pass(const BatchDesc& bd, const SpinorRef& in, const Epi& epi,
-                                                   int use64, double* sh_red, double* sh_col) {
+                                                   int use64, double* sh_wcol, double* sh_col) {
   int cur = -1;                       // first column of the group the sums belong to
   double red[RB];
 #pragma unroll
@@ -357,7 +393,7 @@ __device__ __forceinline__ void batch_stencil_pass(const BatchDesc& bd, const Sp
     const int col0 = sd.col + w.r0;
     if constexpr (Epi::REDUCE) {
       if (col0 != cur) {            // block-uniform: every thread of the tile has the same columns
-        if (cur >= 0) flush_columns<RB>(red, cur, sh_red, sh_col);
+        if (cur >= 0) flush_columns_warp<RB>(red, cur, sh_wcol);
         cur = col0;
 #pragma unroll
         for (int j = 0; j < RB; ++j) red[j] = 0.0;
@@ -390,7 +426,8 @@ __device__ __forceinline__ void batch_stencil_pass(const BatchDesc& bd, const Sp
     }
   }
   if constexpr (Epi::REDUCE) {
-    if (cur >= 0) flush_columns<RB>(red, cur, sh_red, sh_col);
+    if (cur >= 0) flush_columns_warp<RB>(red, cur, sh_wcol);
+    gather_columns(bd.ncols, sh_wcol, sh_col);
   }
 }
 
@@ -399,10 +436,9 @@ __global__ void __launch_bounds__(256, (BatchMinBlocks<T, RB>::value))
     batch_dslash_kernel(BatchDesc bd, SpinorRef in, Epi epi, BatchReduce br, int use64) {
   if (epi.halted()) return;
   __shared__ double sh_col[kMaxCols];
-  __shared__ double sh_red[RB * 32];
-  for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) sh_col[c] = 0.0;
-  __syncthreads();
-  batch_stencil_pass<T, G, SI, DAG, RB, Epi, 1, ONE>(bd, in, epi, use64, sh_red, sh_col);
+  __shared__ double sh_wcol[Epi::REDUCE ? kMaxCols * kMaxWarps : 1];
+  if constexpr (Epi::REDUCE) clear_columns(bd.ncols, sh_wcol);
+  batch_stencil_pass<T, G, SI, DAG, RB, Epi, 1, ONE>(bd, in, epi, use64, sh_wcol, sh_col);
   if constexpr (Epi::REDUCE) {
     auto fin = [&](const double* tot) { epi.finalize_cols(tot, bd.ncols); };
     batch_grid_sum(bd, sh_col, br, fin);
@@ -520,7 +556,7 @@ __device__ __forceinline__ void column_totals(const double* part, int stride, in
 template <GStore G, SStore S, int RB>
 __global__ void __launch_bounds__(256, (BatchMinBlocks<float, RB>::value))
     batch_persistent_kernel(BatchDesc bd, PersistArgs a) {
-  __shared__ double sh_col[kMaxCols], sh_red[RB * 32];
+  __shared__ double sh_col[kMaxCols], sh_wcol[kMaxCols * kMaxWarps];
   __shared__ double s_rr[kMaxCols], s_alpha[kMaxCols], s_beta[kMaxCols], s_tot[kMaxCols];
   __shared__ int s_ok, s_gen;
   BatchState* st = a.st;
@@ -534,11 +570,9 @@ __global__ void __launch_bounds__(256, (BatchMinBlocks<float, RB>::value))
   double* part2 = a.part + (size_t)kMaxCols * a.stride;
   for (int it = 0; it < a.max_iters; ++it) {
     // pass 1: t = M p, |t|^2 per column -> alpha
-    for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) sh_col[c] = 0.0;
-    __syncthreads();
+    clear_columns(bd.ncols, sh_wcol);
     PEpiCG1<S> e1{a.tlo, bd.total};
-    batch_stencil_pass<float, G, S, false, RB, PEpiCG1<S>, 2>(bd, a.plo, e1, 0, sh_red, sh_col);
-    __syncthreads();
+    batch_stencil_pass<float, G, S, false, RB, PEpiCG1<S>, 2>(bd, a.plo, e1, 0, sh_wcol, sh_col);
     for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) part1[(size_t)c * a.stride + blockIdx.x] = sh_col[c];
     if (!grid_barrier(a, gen, &s_ok)) return;
     column_totals(part1, a.stride, bd.ncols, s_tot);
@@ -557,11 +591,9 @@ __global__ void __launch_bounds__(256, (BatchMinBlocks<float, RB>::value))
       return;
     }
     // pass 2: r -= alpha M^dag t, x += alpha p, |r|^2 per column -> beta, halt decision
-    for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) sh_col[c] = 0.0;
-    __syncthreads();
+    clear_columns(bd.ncols, sh_wcol);
     PEpiCG2<S> e2{a.rlo, a.xlo, a.plo, bd.total, s_alpha};
-    batch_stencil_pass<float, G, S, true, RB, PEpiCG2<S>, 2>(bd, a.tlo, e2, 0, sh_red, sh_col);
-    __syncthreads();
+    batch_stencil_pass<float, G, S, true, RB, PEpiCG2<S>, 2>(bd, a.tlo, e2, 0, sh_wcol, sh_col);
     for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) part2[(size_t)c * a.stride + blockIdx.x] = sh_col[c];
     if (!grid_barrier(a, gen, &s_ok)) return;
     column_totals(part2, a.stride, bd.ncols, s_tot);

@@ -368,6 +368,9 @@ def test_device_loop_matches_host_loop(lq, df):
                 ctxs.append(c)
             lq.lq_set_option(ctxs[0], lq.LQ_OPT_DF64_UPDATES, df)
             lq.lq_set_option(ctxs[0], lq.LQ_OPT_BATCH_DEVICE_LOOP, loop)
+            # one fixed launch shape for both (the tuner's timing may pick different shapes,
+            # whose reductions round differently)
+            lq.lq_set_option(ctxs[0], lq.LQ_OPT_BATCH_RHS_PER_THREAD, 1)
             xs = [torch.zeros_like(dev(p)) for p in phis]
             status, st, iters, resid, hist = lq.lq_solve_batch(ctxs, xs, [dev(p) for p in phis], kappas, R, 1e-10,
                                                                5000, lq.LQ_F16_12, 25, hist_len=2000)

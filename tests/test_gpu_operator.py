@@ -118,6 +118,40 @@ def test_apply_MdagM_f64_and_host_buffers(lq):
     assert np.array_equal(Uback, U)
 
 
+@pytest.mark.parametrize("dims", [(4, 2, 4, 6), (5, 3, 7, 5)])
+def test_page_locked_host_buffers_in_place(lq, dims):
+    """With LQ_OPT_HOST_DIRECT the packing kernels read and write page-locked host buffers in
+    place: gauge in and out, right-hand side in, result out, and a solve, all bit-identical
+    to the staged path; pageable host buffers are still staged.  Volumes that are not a
+    multiple of the packing tiles (64 sites for links, 128 for spinors) cover the ragged
+    tile."""
+    lat, U, psi = _setup(dims, seed=4)
+    Up, psip = torch.from_numpy(U).pin_memory(), torch.from_numpy(psi).pin_memory()
+    res = {}
+    for direct in (0, 1):
+        ctx = lq.lq_create(dims)
+        try:
+            lq.lq_set_option(ctx, lq.LQ_OPT_HOST_DIRECT, direct)
+            lq.lq_gauge_set(ctx, Up)
+            out_p = torch.empty_like(psip).pin_memory()
+            lq.lq_apply_MdagM(ctx, out_p, psip, 0.14)
+            out_n = np.empty_like(psi)
+            lq.lq_apply_MdagM(ctx, out_n, psi, 0.14)                    # pageable: staged
+            Ub = torch.empty_like(Up).pin_memory()
+            lq.lq_gauge_get(ctx, Ub)
+            x = torch.zeros_like(psip).pin_memory()
+            status, st = lq.lq_solve_MdagM(ctx, x, psip, 0.14, 1e-10, 5000, lq.LQ_F16_12, 50)
+            assert status == lq.LQ_OK
+            res[direct] = (out_p.numpy().copy(), out_n, Ub.numpy().copy(), x.numpy().copy())
+        finally:
+            lq.lq_destroy(ctx)
+    ref = o_apply_MdagM(U, psi, dims, 0.14)
+    assert rel_err(res[1][0], ref) < 1e-12
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(res[1][2], U)
+
+
 def test_free_field_plane_wave(lq):
     """U = 1: the GPU operator reproduces the closed form on a plane wave."""
     dims = (4, 6, 2, 8)
