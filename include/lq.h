@@ -161,6 +161,11 @@ lq_status lq_set_stream(lq_ctx* ctx, void* cuda_stream);
  *                       host waits once.  Each loop stops at a cap taken from maxiter.
  *                       0: the host launches a graph of reliable_every iterations, runs the
  *                       reliable update and reads the state back once per chunk.
+ *   LQ_OPT_BATCH_TILE_ORDER  0 (default): the autotuner of lq_solve_batch tries both tile orders;
+ *                       1: site-major only (the right-hand-side groups of one site tile are
+ *                       consecutive tiles); 2: group-major only (every site tile of one group,
+ *                       then the next).  With LQ_OPT_BATCH_RHS_PER_THREAD set, 0 and 1 mean
+ *                       site-major.  Changing it drops the batch workspace of the context.
  *   LQ_OPT_HOST_DIRECT  1 (default): page-locked host buffers mapped into the device's address
  *                       space are read (gauge field, right-hand sides) and written (solutions,
  *                       lq_gauge_get) in place by the packing kernels, which access the
@@ -174,7 +179,7 @@ lq_status lq_set_stream(lq_ctx* ctx, void* cuda_stream);
  *                       LQ_ERR_TIMEOUT path (tests of the failure detection only). */
 enum { LQ_OPT_CUDA_GRAPHS = 1, LQ_OPT_DF64_UPDATES = 2, LQ_OPT_PAIR_SITES = 3, LQ_OPT_STAGED = 4,
        LQ_OPT_BATCH_RHS_PER_THREAD = 5, LQ_OPT_BATCH_PERSISTENT = 6, LQ_OPT_BATCH_BARRIER_TEST = 7,
-       LQ_OPT_BATCH_DEVICE_LOOP = 8, LQ_OPT_HOST_DIRECT = 9 };
+       LQ_OPT_BATCH_DEVICE_LOOP = 8, LQ_OPT_HOST_DIRECT = 9, LQ_OPT_BATCH_TILE_ORDER = 10 };
 lq_status lq_set_option(lq_ctx* ctx, int option, int value);
 
 /* Number of lattice sites V. */

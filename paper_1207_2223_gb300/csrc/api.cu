@@ -681,6 +681,11 @@ lq_status lq_set_option(lq_ctx* c, int option, int value) {
     case LQ_OPT_BATCH_PERSISTENT: c->batch_persistent = value ? 1 : 0; return LQ_OK;
     case LQ_OPT_BATCH_DEVICE_LOOP: c->batch_device_loop = value ? 1 : 0; return LQ_OK;
     case LQ_OPT_HOST_DIRECT: c->host_direct = value ? 1 : 0; return LQ_OK;
+    case LQ_OPT_BATCH_TILE_ORDER:
+      if (value < 0 || value > 2) return fail(c, LQ_ERR_ARG, "tile order is 0 (tuned), 1 or 2");
+      c->batch_order = value;
+      if (c->batch) { destroy_batch_work(c->batch); c->batch = nullptr; }
+      return LQ_OK;
     case LQ_OPT_BATCH_BARRIER_TEST:
       if (value < 0 || value > 1) return fail(c, LQ_ERR_ARG, "barrier test option is 0 or 1");
       c->batch_barrier_extra = value;

@@ -656,12 +656,13 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
     w->tune.tile = 256;
     w->tune.rb = c->batch_rb;
     w->tune.per_sm = 0;
-    w->tune.site_major = 1;
+    w->tune.site_major = c->batch_order == 2 ? 0 : 1;
     w->tune_ms.clear();
   }
   if (w->tune.tile == 0) {
     std::vector<Tuning> cand;
-    for (int order : {1, 0})
+    for (int order : {1, 0}) {
+      if (c->batch_order != 0 && (c->batch_order == 1) != (order == 1)) continue;   // order fixed
       for (int rb : {1, 2, 3, 4})
         if (nrhs % rb == 0)
           for (int tile : {256, 128})
@@ -674,6 +675,7 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
               t.site_major = order;
               cand.push_back(t);
             }
+    }
     batch_init(w, bdi, inner_prec, st);
     // a state that never halts (no tolerance, no reliable-update trigger, no limit), reset
     // before every candidate, so that every candidate times full iterations

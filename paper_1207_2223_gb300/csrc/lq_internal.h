@@ -116,6 +116,7 @@ struct lq_ctx {
   int batch_persistent = 0;              // batched solves: one cooperative launch per chunk of iterations
   int batch_barrier_extra = 0;           // batched solves: phantom blocks the barrier waits for (timeout tests)
   int batch_device_loop = 1;             // batched solves: the whole solve as one graph with conditional nodes
+  int batch_order = 0;                   // batched solves: tile order (0 tuned, 1 site-major, 2 group-major)
   int host_direct = 1;                   // kernels read / write mapped page-locked host buffers in place
 };
 

@@ -173,6 +173,7 @@ LQ_OPT_CUDA_GRAPHS, LQ_OPT_DF64_UPDATES, LQ_OPT_PAIR_SITES, LQ_OPT_STAGED = 1, 2
 LQ_OPT_BATCH_RHS_PER_THREAD, LQ_OPT_BATCH_PERSISTENT, LQ_OPT_BATCH_BARRIER_TEST = 5, 6, 7
 LQ_OPT_BATCH_DEVICE_LOOP = 8
 LQ_OPT_HOST_DIRECT = 9
+LQ_OPT_BATCH_TILE_ORDER = 10
 
 
 def lq_set_option(ctx, option, value):

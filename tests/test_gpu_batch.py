@@ -157,12 +157,13 @@ def test_full_size_uneven_lattices(lq):
             lq.lq_destroy(c)
 
 
+@pytest.mark.parametrize("order", [1, 2])
 @pytest.mark.parametrize("rb", [1, 2, 3, 4])
 @pytest.mark.parametrize("prec", [2, 3, 4, 6])
-def test_rhs_per_thread_variants_match_oracle(lq, rb, prec):
-    """Every register-blocking width (right-hand sides per thread, forced) solves a 12-RHS
-    batch at 4^3 x 8 to a 1e-10 FP64 true residual, agrees with the oracle's solutions, and
-    the per-column residual histories start at 1 and fall below 1e-6."""
+def test_rhs_per_thread_variants_match_oracle(lq, rb, prec, order):
+    """Every register-blocking width (right-hand sides per thread, forced) in both tile orders
+    solves a 12-RHS batch at 4^3 x 8 to a 1e-10 FP64 true residual, agrees with the oracle's
+    solutions, and the per-column residual histories start at 1 and fall below 1e-6."""
     dims, R, kappa = (4, 4, 4, 8), 12, 0.15
     lat = Lattice(dims)
     U = gauge_exp_iA(lat, 0.3, 5)
@@ -170,6 +171,7 @@ def test_rhs_per_thread_variants_match_oracle(lq, rb, prec):
     ctx = lq.lq_create(dims)
     try:
         lq.lq_set_option(ctx, lq.LQ_OPT_BATCH_RHS_PER_THREAD, rb)
+        lq.lq_set_option(ctx, lq.LQ_OPT_BATCH_TILE_ORDER, order)
         lq.lq_gauge_set(ctx, dev(U))
         x = torch.zeros_like(dev(phis))
         status, st, iters, resid, hist = lq.lq_solve_batch([ctx], [x], [dev(phis)], [kappa], R, 1e-10, 5000, prec,
@@ -179,7 +181,7 @@ def test_rhs_per_thread_variants_match_oracle(lq, rb, prec):
     finally:
         lq.lq_destroy(ctx)
     assert status == lq.LQ_OK and np.all(resid <= 1e-10)
-    assert tune["rhs_per_thread"] == rb and tune["tile"] == 256 and tune["site_major"] == 1
+    assert tune["rhs_per_thread"] == rb and tune["tile"] == 256 and tune["site_major"] == (1 if order == 1 else 0)
     for i in (0, 7, 11):
         xr, _, _ = cg_MdagM(U, phis[i], dims, kappa, 1e-13)
         assert rel_err(xs[i], xr) < X_TOL
