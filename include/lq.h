@@ -148,7 +148,8 @@ lq_status lq_set_stream(lq_ctx* ctx, void* cuda_stream);
  *                       divide nrhs), 256 threads per block, no timing.  Changing it drops
  *                       the batch workspace of the context.
  *   LQ_OPT_BATCH_PERSISTENT  0 (default): lq_solve_batch runs its iterations as CUDA graphs of
- *                       one launch per CG pass; 1: one persistent cooperative launch per chunk
+ *                       one launch per CG pass (LQ_OPT_BATCH_DEVICE_LOOP says how the host
+ *                       drives them); 1: one persistent cooperative launch per chunk
  *                       of reliable_every iterations runs every pass of every iteration, with
  *                       device-wide barriers between the passes.  The barrier waits are
  *                       bounded (about one second); a wait that runs out makes the call
@@ -239,16 +240,19 @@ lq_status lq_solve_MdagM(lq_ctx* ctx, double* x, const double* phi, double kappa
  * layout).  Right-hand sides of one system share its links, which are read
  * once per site for all of them: a thread applies each decoded link to several right-hand
  * sides held in registers.  Iterations run in FP32 arithmetic on the storage
- * of inner_prec (LQ_F32, LQ_F32_12, LQ_F16_12, LQ_BF16_12 or LQ_I16_12) with FP64 reliable updates
+ * of inner_prec (LQ_F32, LQ_F32_12, LQ_F16_12, LQ_BF16_12 or LQ_I16_12) with reliable updates
  * every reliable_every iterations (sooner when a column's iterated residual fell by 1e-2,
  * 16-bit storage, or 1e-3, FP32; a column whose true residual turns out far above its
- * iterated one restarts its search direction);
- * a column (system x right-hand side) whose FP64 true residual meets tol is
- * frozen.  1 <= n <= 16, 1 <= nrhs <= 16, n * nrhs <= 64.  The launch shape (threads
- * per block, right-hand sides per thread, resident blocks per SM) is picked by timing
- * the candidates on the first call for a batch shape (autotuning; lq_batch_tuning
- * reports the choice); the iterations run as CUDA graphs on ctxs[0]'s stream, which
- * owns the workspace.
+ * iterated one restarts its search direction): double-float updates per column
+ * (LQ_OPT_DF64_UPDATES of ctxs[0]), and once every column meets tol an FP64
+ * certification that reopens any column whose FP64 true residual misses it; the solve
+ * ends when every column's FP64 true residual meets tol.  1 <= n <= 16, 1 <= nrhs <= 16,
+ * n * nrhs <= 64.  The launch shape (tile order, threads per block, right-hand sides per
+ * thread, resident blocks per SM) is picked by timing the candidates on the first call
+ * for a batch shape (autotuning; lq_batch_tuning reports the choice).  Everything runs on
+ * ctxs[0]'s stream, which owns the workspace: by default the whole solve as one CUDA
+ * graph with conditional nodes (LQ_OPT_BATCH_DEVICE_LOOP), or per-chunk graphs, or
+ * persistent launches (LQ_OPT_BATCH_PERSISTENT).
  *   hist     optional host array [n * nrhs][hist_len]: relative iterated residual
  *            of every column per iteration
  *   iters    optional host int[n * nrhs]: iterations until each column was frozen
