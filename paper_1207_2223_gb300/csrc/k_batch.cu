@@ -47,10 +47,20 @@
 
 namespace lq {
 
-// p = r + beta_col p (inner format), skipped when halted unless forced
+// p = r + beta_col p (inner format), skipped when halted unless forced.  use_cond: the
+// last kernel of an iteration inside the device-side loop; before anything else one thread
+// sets the loop's condition (another iteration unless this one raised halt, counted against
+// the iteration limit so that the loop ends even if the state never halts).
 template <SStore S>
-__global__ void batch_xpay_kernel(BatchDesc bd, SpinorRef r, SpinorRef p, const BatchState* st, int forced) {
-  if (!forced && *(volatile const int*)&st->halt) return;
+__global__ void batch_xpay_kernel(BatchDesc bd, SpinorRef r, SpinorRef p, BatchState* st, int forced,
+                                  cudaGraphConditionalHandle cond, int use_cond) {
+  const int halted = *(volatile const int*)&st->halt;
+  if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int g = ++st->guard_inner;
+    st->loops[0]++;
+    cudaGraphSetConditional(cond, (!halted && g <= st->maxiter) ? 1u : 0u);
+  }
+  if (!forced && halted) return;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < bd.total; e += gridDim.x * blockDim.x) {
     const SysDesc& sd = bd.sys[system_of_element(bd, e)];
     const float beta = (float)st->beta[sd.col + (e - sd.off) / sd.geo.V];
@@ -66,13 +76,19 @@ __global__ void batch_xpay_kernel(BatchDesc bd, SpinorRef r, SpinorRef p, const 
   }
 }
 
-void launch_batch_xpay(const BatchDesc& bd, SStore s, SpinorRef r, SpinorRef p, const BatchState* st, int forced,
-                       int grid, cudaStream_t stream) {
+void launch_batch_xpay(const BatchDesc& bd, SStore s, SpinorRef r, SpinorRef p, BatchState* st, int forced,
+                       int grid, cudaStream_t stream, cudaGraphConditionalHandle cond, int use_cond) {
   switch (s) {
-    case SStore::F16: batch_xpay_kernel<SStore::F16><<<grid, 256, 0, stream>>>(bd, r, p, st, forced); break;
-    case SStore::BF16: batch_xpay_kernel<SStore::BF16><<<grid, 256, 0, stream>>>(bd, r, p, st, forced); break;
-    case SStore::I16: batch_xpay_kernel<SStore::I16><<<grid, 256, 0, stream>>>(bd, r, p, st, forced); break;
-    default: batch_xpay_kernel<SStore::F32><<<grid, 256, 0, stream>>>(bd, r, p, st, forced); break;
+    case SStore::F16:
+      batch_xpay_kernel<SStore::F16><<<grid, 256, 0, stream>>>(bd, r, p, st, forced, cond, use_cond);
+      break;
+    case SStore::BF16:
+      batch_xpay_kernel<SStore::BF16><<<grid, 256, 0, stream>>>(bd, r, p, st, forced, cond, use_cond);
+      break;
+    case SStore::I16:
+      batch_xpay_kernel<SStore::I16><<<grid, 256, 0, stream>>>(bd, r, p, st, forced, cond, use_cond);
+      break;
+    default: batch_xpay_kernel<SStore::F32><<<grid, 256, 0, stream>>>(bd, r, p, st, forced, cond, use_cond); break;
   }
 }
 
@@ -122,8 +138,8 @@ __global__ void batch_init_kernel(BatchDesc bd, SpinorRef phi64, SpinorRef x64, 
     }
   }
   if (cur >= 0) flush_columns<RB>(red, cur, sh_red, sh_col);
-  auto fin = [&](const double* tot) {
-    for (int c = 0; c < bd.ncols; ++c) {
+  auto fin = [&](const double* tot) {       // every thread of the last block: one column each
+    for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) {
       st->phi2[c] = tot[c];
       st->rr[c] = st->rr_prev[c] = st->rr_true[c] = st->rr_ref[c] = tot[c];
       st->done[c] = tot[c] == 0.0 ? 1 : 0;
@@ -283,8 +299,12 @@ BatchIterArgs iter_args(const BatchWork* w, const Tuning& tu) {
   return BatchIterArgs{w->plo.ref(), w->tlo.ref(), w->rlo.ref(), w->xlo.ref(), w->st, w->br, w->sms, tu.per_sm};
 }
 
-void batch_iteration_prec(BatchWork* w, const BatchDesc& bd, int prec, const Tuning& tu, cudaStream_t st) {
-  const BatchIterArgs a = iter_args(w, tu);
+// use_cond: inside the device-side loop, whose condition the iteration's last kernel sets
+void batch_iteration_prec(BatchWork* w, const BatchDesc& bd, int prec, const Tuning& tu, cudaStream_t st,
+                          cudaGraphConditionalHandle cond = 0, int use_cond = 0) {
+  BatchIterArgs a = iter_args(w, tu);
+  a.cond = cond;
+  a.use_cond = use_cond;
   switch (prec) {
     case LQ_F16_12: batch_iteration_h16(a, bd, prec, st); break;
     case LQ_BF16_12: batch_iteration_bf16(a, bd, prec, st); break;
@@ -332,7 +352,7 @@ template <SStore S>
 void batch_reliable_tail_s(BatchWork* w, const BatchDesc& bd, const BatchDesc& bd64, bool fold, cudaStream_t st) {
   if (fold) batch_accumulate_kernel<S><<<flat_grid(w), 256, 0, st>>>(bd.total, w->xlo.ref(), w->x64.ref());
   batch_true_residual_s<S>(w, bd64, st);
-  batch_xpay_kernel<S><<<flat_grid(w), 256, 0, st>>>(bd, w->rlo.ref(), w->plo.ref(), w->st, 1);
+  batch_xpay_kernel<S><<<flat_grid(w), 256, 0, st>>>(bd, w->rlo.ref(), w->plo.ref(), w->st, 1, 0, 0);
 }
 void batch_reliable_tail(BatchWork* w, const BatchDesc& bd, const BatchDesc& bd64, int prec, bool fold,
                          cudaStream_t st) {
@@ -364,12 +384,6 @@ Geom flat_geom(int total) {
 __global__ void cond_enter_kernel(BatchState* st, cudaGraphConditionalHandle inner) {
   st->guard_inner = 0;
   cudaGraphSetConditional(inner, st->halt ? 0u : 1u);
-}
-// after a CG iteration: another one unless it raised halt
-__global__ void cond_iterate_kernel(BatchState* st, cudaGraphConditionalHandle inner) {
-  const int g = ++st->guard_inner;
-  st->loops[0]++;
-  cudaGraphSetConditional(inner, (!st->halt && g <= st->maxiter) ? 1u : 0u);
 }
 // the double-float residual unless every open column's iterated residual met the
 // tolerance (that update goes straight to the FP64 certification)
@@ -482,8 +496,7 @@ cudaError_t build_solve_graph(BatchWork* w, const BatchDesc& bd, const BatchDesc
       e = add_conditional(s, cudaGraphCondTypeWhile, h_inner, &body);
       if (e != cudaSuccess) return e;
       e = record_body(s2, body, [&](cudaStream_t q) -> cudaError_t {
-        batch_iteration_prec(w, bd, prec, tu, q);
-        cond_iterate_kernel<<<1, 1, 0, q>>>(st, h_inner);
+        batch_iteration_prec(w, bd, prec, tu, q, h_inner, 1);   // its last kernel sets h_inner
         return cudaSuccess;
       });
       if (e != cudaSuccess) return e;
@@ -772,10 +785,10 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
         break;
       }
     }
-    // launches from the loop counts: an iteration is three passes and its condition; an
-    // update cycle enters and leaves the loop around its update
+    // launches from the loop counts: an iteration is three passes (the last one sets the
+    // loop's condition); an update cycle enters and leaves the loop around its update
     const int* L = w->st_host->loops;
-    s.kernel_launches += 4 * L[0];
+    s.kernel_launches += 3 * L[0];
     if (dfru) {
       s.kernel_launches += 5 * L[1] + (2 * bd.ncols + 1) * L[2] + 4 * L[3];
       s.reliable_updates += L[2] + L[3];

@@ -94,8 +94,23 @@ __device__ __forceinline__ TileWork tile_work(const BatchDesc& bd, int t) {
   return {k, g * bd.rb, st * bd.tile + (int)threadIdx.x};
 }
 
+// Column totals of one pass: warp w sums columns w, w + nwarps, ...; lane l adds blocks
+// l, l + 32, ... and the warp adds the lanes in a fixed tree: the same in every block.
+__device__ __forceinline__ void column_totals(const double* part, int stride, int ncols, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < ncols; c += nw) {
+    double x = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) x += __ldcg(part + (size_t)c * stride + b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) out[c] = x;
+  }
+}
+
 // Column sums of one block (sh_col[ncols]) -> partials; the last block adds
-// them up per column and calls fin(col_totals) in thread 0.
+// them up per column (column_totals: a warp per column, fixed order) and calls
+// fin(col_totals) in every one of its threads (finalisers spread the columns over
+// the threads and vote on block-wide decisions).
 template <class Fin>
 __device__ void batch_grid_sum(const BatchDesc& bd, double* sh_col, const BatchReduce& br, const Fin& fin) {
   __shared__ bool last;
@@ -109,16 +124,10 @@ __device__ void batch_grid_sum(const BatchDesc& bd, double* sh_col, const BatchR
   if (!last) return;
   __threadfence();
   __shared__ double tot[kMaxCols];
-  for (int c = threadIdx.x; c < bd.ncols; c += blockDim.x) {
-    double a = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) a += __ldcg(br.partials + (size_t)c * br.max_blocks + b);
-    tot[c] = a;
-  }
+  column_totals(br.partials, br.max_blocks, bd.ncols, tot);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    fin(tot);
-    *br.ticket = 0u;
-  }
+  fin(tot);
+  if (threadIdx.x == 0) *br.ticket = 0u;
 }
 
 // Adds the block's per-thread sums v[0..RB) to columns col0 .. col0 + RB - 1 of
@@ -196,13 +205,16 @@ struct BEpiCG1 {                             // t = M p, tt = |t|^2, alpha = rr 
     for (int k = 0; k < 12; ++k) { a = fma(v[k].re, v[k].re, a); a = fma(v[k].im, v[k].im, a); }
     return (double)a;
   }
+  // every thread of the reducing block: one column per thread
   __device__ void finalize_cols(const double* tot, int ncols) const {
-    for (int c = 0; c < ncols; ++c) {
+    int bad = 0;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
       if (st->done[c]) { st->alpha[c] = 0.0; continue; }
       const double tt = tot[c];
-      if (!(tt > 0.0) || !isfinite(tt)) { st->breakdown = 1; st->halt = 1; st->alpha[c] = 0.0; }
+      if (!(tt > 0.0) || !isfinite(tt)) { bad = 1; st->alpha[c] = 0.0; }
       else st->alpha[c] = st->rr[c] / tt;
     }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) { st->breakdown = 1; st->halt = 1; }
   }
 };
 
@@ -233,25 +245,33 @@ struct BEpiCG2 {                             // r -= alpha M^dag t, x += alpha p
     store_spinor<xlo_store(S), T>(x, total, e, xv);
     return (double)a;
   }
+  // every thread of the reducing block: one column per thread, block-wide votes
   __device__ void finalize_cols(const double* tot, int ncols) const {
     const int it = st->iter;
-    bool all_below = true;
-    for (int c = 0; c < ncols; ++c) {
+    int above = 0, trigger = 0, bad = 0;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
       if (st->hist && it < st->hist_len) st->hist[(size_t)c * st->hist_len + it] = sqrt(tot[c] / st->phi2[c]);
       if (st->done[c]) { st->beta[c] = 0.0; continue; }
       const double rr_new = tot[c];
-      if (!isfinite(rr_new)) { st->breakdown = 1; st->halt = 1; }
+      if (!isfinite(rr_new)) bad = 1;
       st->beta[c] = rr_new / st->rr[c];
       st->rr_prev[c] = st->rr[c];
       st->rr[c] = rr_new;
-      if (rr_new > st->stop2 * st->phi2[c]) all_below = false;
-      if (rr_new < st->delta2 * st->rr_ref[c]) st->halt = 1;     // fell far: reliable update due
+      if (rr_new > st->stop2 * st->phi2[c]) above = 1;
+      if (rr_new < st->delta2 * st->rr_ref[c]) trigger = 1;      // fell far: reliable update due
     }
-    st->iter = it + 1;
-    st->iter_since_ru += 1;
-    if (all_below) st->halt = 1;
-    if (st->ru_every > 0 && st->iter_since_ru >= st->ru_every) st->halt = 1;
-    if (st->iter >= st->maxiter) st->halt = 1;
+    above = __syncthreads_or(above);
+    trigger = __syncthreads_or(trigger);
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+      const int since = st->iter_since_ru + 1;
+      st->iter = it + 1;
+      st->iter_since_ru = since;
+      if (bad) st->breakdown = 1;
+      if (bad || trigger || !above) st->halt = 1;
+      if (st->ru_every > 0 && since >= st->ru_every) st->halt = 1;
+      if (it + 1 >= st->maxiter) st->halt = 1;
+    }
   }
 };
 
@@ -301,10 +321,13 @@ struct BEpiResidual {                        // r64 = phi - M^dag tmp, r_lo = r6
     store_spinor<S, double>(rlo, total, e, rv);
     return a;
   }
+  // every thread of the reducing block: one column per thread
   __device__ void finalize_cols(const double* tot, int ncols) const {
-    for (int c = 0; c < ncols; ++c) reliable_update_column(st, c, tot[c]);
-    st->iter_since_ru = 0;
-    st->halt = 0;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) reliable_update_column(st, c, tot[c]);
+    if (threadIdx.x == 0) {
+      st->iter_since_ru = 0;
+      st->halt = 0;
+    }
   }
 };
 
@@ -540,19 +563,6 @@ __device__ __forceinline__ bool grid_barrier(const PersistArgs& a, unsigned int&
   return *s_ok != 0;
 }
 
-// Column totals of one pass: warp w sums columns w, w + nwarps, ...; lane l adds blocks
-// l, l + 32, ... and the warp adds the lanes in a fixed tree: the same in every block.
-__device__ __forceinline__ void column_totals(const double* part, int stride, int ncols, double* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int c = warp; c < ncols; c += nw) {
-    double x = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) x += __ldcg(part + (size_t)c * stride + b);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) out[c] = x;
-  }
-}
-
 template <GStore G, SStore S, int RB>
 __global__ void __launch_bounds__(256, (BatchMinBlocks<float, RB>::value))
     batch_persistent_kernel(BatchDesc bd, PersistArgs a) {
@@ -678,6 +688,8 @@ struct BatchIterArgs {
   BatchReduce br;
   int sms;        // SMs of the device
   int per_sm;     // resident blocks per SM used by the stencil passes (0: all that fit)
+  cudaGraphConditionalHandle cond = 0;   // the device-side loop's condition (use_cond != 0)
+  int use_cond = 0;
 };
 
 template <typename T, GStore G, SStore SI, bool DAG, int RB, class Epi, bool ONE>
@@ -715,9 +727,10 @@ void launch_batch(const BatchDesc& bd, SpinorRef in, const Epi& epi, const Batch
   }
 }
 
-// p = r + beta_col p (inner format), skipped when halted unless forced
-void launch_batch_xpay(const BatchDesc& bd, SStore s, SpinorRef r, SpinorRef p, const BatchState* st, int forced,
-                       int grid, cudaStream_t stream);
+// p = r + beta_col p (inner format), skipped when halted unless forced; use_cond: also sets
+// the device-side iteration loop's condition cond
+void launch_batch_xpay(const BatchDesc& bd, SStore s, SpinorRef r, SpinorRef p, BatchState* st, int forced,
+                       int grid, cudaStream_t stream, cudaGraphConditionalHandle cond = 0, int use_cond = 0);
 
 // One CG iteration (t = M p; r -= alpha M^dag t, x += alpha p; p = r + beta p) of the batch
 // in the given storage, one translation unit per format (k_batch_f32.cu FP32-18,
@@ -758,7 +771,7 @@ void batch_iteration_t(const BatchIterArgs& a, const BatchDesc& bd, cudaStream_t
   launch_batch<float, G, S, false>(bd, a.plo, e1, a.br, 0, a.sms, a.per_sm, st);
   BEpiCG2<S> e2{a.rlo, a.xlo, a.plo, bd.total, a.st};
   launch_batch<float, G, S, true>(bd, a.tlo, e2, a.br, 0, a.sms, a.per_sm, st);
-  launch_batch_xpay(bd, S, a.rlo, a.plo, a.st, 0, a.sms * 8, st);
+  launch_batch_xpay(bd, S, a.rlo, a.plo, a.st, 0, a.sms * 8, st, a.cond, a.use_cond);
 }
 
 }  // namespace lq

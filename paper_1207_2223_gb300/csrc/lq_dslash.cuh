@@ -222,14 +222,14 @@ struct EpiCG1 {
     red[0] += site_norm2(v);
   }
   __device__ void finalize(double (&tot)[NRED]) const {
-    const double tt = tot[0];
+    const double tt = tot[0], rr = st->rr;
     st->tt = tt;
-    if (!(tt > 0.0) || !isfinite(tt) || !isfinite(st->rr)) {
+    if (!(tt > 0.0) || !isfinite(tt) || !isfinite(rr)) {
       st->breakdown = 1;
       st->halt = 1;
       st->alpha = 0.0;
     } else {
-      st->alpha = st->rr / tt;
+      st->alpha = rr / tt;
     }
   }
 };
@@ -261,20 +261,25 @@ struct EpiCG2 {
     store_spinor<SX, T>(x, V, s, xv);
     red[0] += site_norm2(rv);
   }
+  // One thread, at the end of the kernel's critical path: every field is read before
+  // the first store (a store through st->hist could alias them and serialise the reads).
   __device__ void finalize(double (&tot)[NRED]) const {
     const double rr_new = tot[0];
-    const int it = st->iter;
-    if (st->hist != nullptr && it < st->hist_len) st->hist[it] = sqrt(rr_new / st->phi2);
+    const int it = st->iter, since = st->iter_since_ru + 1, ru_every = st->ru_every, maxiter = st->maxiter;
+    const int hist_len = st->hist_len;
+    const double rr = st->rr, phi2 = st->phi2, stop2 = st->stop2, delta2 = st->delta2, rr_ref = st->rr_ref;
+    double* hist = st->hist;
+    const bool finite = isfinite(rr_new);
+    const bool halt = !finite || rr_new <= stop2 || (ru_every > 0 && since >= ru_every) ||
+                      (delta2 > 0.0 && rr_new < delta2 * rr_ref) || it + 1 >= maxiter;
     st->iter = it + 1;
-    st->iter_since_ru += 1;
-    st->beta = rr_new / st->rr;
-    st->rr_prev = st->rr;
+    st->iter_since_ru = since;
+    st->beta = rr_new / rr;
+    st->rr_prev = rr;
     st->rr = rr_new;
-    if (!isfinite(rr_new)) { st->breakdown = 1; st->halt = 1; return; }
-    if (rr_new <= st->stop2) st->halt = 1;
-    if (st->ru_every > 0 && st->iter_since_ru >= st->ru_every) st->halt = 1;
-    if (st->delta2 > 0.0 && rr_new < st->delta2 * st->rr_ref) st->halt = 1;
-    if (st->iter >= st->maxiter) st->halt = 1;
+    if (!finite) st->breakdown = 1;
+    if (halt) st->halt = 1;
+    if (hist != nullptr && it < hist_len) hist[it] = sqrt(rr_new / phi2);
   }
 };
 

@@ -393,3 +393,36 @@ def test_device_loop_matches_host_loop(lq, df):
     assert s1["converged"] == s0["converged"] == 1
     xr, _, _ = cg_MdagM(Us[1], phis[1][0], shapes[1], kappas[1], 1e-13)
     assert rel_err(x1[1][0], xr) < X_TOL
+
+
+@pytest.mark.parametrize("loop,df", [(1, 1), (0, 1), (1, 0)])
+def test_zero_and_non_finite_columns(lq, loop, df):
+    """Degenerate columns: a zero right-hand side is frozen at once (x = 0, residual 0) while the
+    other columns converge; a NaN in one right-hand side ends the call with LQ_ERR_NAN (no hang,
+    whichever loop drives it), and the context then solves normally."""
+    dims, R = (4, 4, 2, 4), 3
+    lat = Lattice(dims)
+    phis = np.stack([source(lat, 8, i) for i in range(R)])
+    phis[1] = 0.0
+    ctx = lq.lq_create(dims)
+    try:
+        lq.lq_gauge_set(ctx, dev(gauge_exp_iA(lat, 0.3, 8)))
+        lq.lq_set_option(ctx, lq.LQ_OPT_BATCH_DEVICE_LOOP, loop)
+        lq.lq_set_option(ctx, lq.LQ_OPT_DF64_UPDATES, df)
+        x = torch.zeros_like(dev(phis))
+        status, st, iters, resid, _ = lq.lq_solve_batch([ctx], [x], [dev(phis)], [0.15], R, 1e-10, 5000,
+                                                        lq.LQ_F16_12, 25)
+        assert status == lq.LQ_OK and st["converged"] == 1
+        assert resid[1] == 0.0 and np.all(resid <= 1e-10)
+        assert not torch.any(x[1] != 0)
+        bad = phis.copy()
+        bad[2, 5, 1, 2] = np.nan
+        with pytest.raises(lq.LQError) as e:
+            lq.lq_solve_batch([ctx], [torch.zeros_like(x)], [dev(bad)], [0.15], R, 1e-10, 5000, lq.LQ_F16_12, 25)
+        assert e.value.status == lq.LQ_ERR_NAN
+        x2 = torch.zeros_like(x)
+        status, st, iters, resid2, _ = lq.lq_solve_batch([ctx], [x2], [dev(phis)], [0.15], R, 1e-10, 5000,
+                                                         lq.LQ_F16_12, 25)
+        assert status == lq.LQ_OK and np.array_equal(resid2, resid) and torch.equal(x2, x)
+    finally:
+        lq.lq_destroy(ctx)
