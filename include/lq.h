@@ -167,6 +167,12 @@ lq_status lq_set_stream(lq_ctx* ctx, void* cuda_stream);
  *                       consecutive tiles); 2: group-major only (every site tile of one group,
  *                       then the next).  With LQ_OPT_BATCH_RHS_PER_THREAD set, 0 and 1 mean
  *                       site-major.  Changing it drops the batch workspace of the context.
+ *   LQ_OPT_DF64_PREFETCH  0 (default): the double-float operator (LQ_DF64 applications and the
+ *                       double-float reliable updates) loads each hop's links and spinors as
+ *                       it needs them; 1: a variant that copies the next hop's operands into
+ *                       shared memory with asynchronous copies while the current hop computes.
+ *                       Same arithmetic in the same order: identical results.  Measured slower
+ *                       on GB300 (1.64 against 1.50 ms at 32^3 x 64), so off.
  *   LQ_OPT_HOST_DIRECT  1 (default): page-locked host buffers mapped into the device's address
  *                       space are read (gauge field, right-hand sides) and written (solutions,
  *                       lq_gauge_get) in place by the packing kernels, which access the
@@ -180,7 +186,8 @@ lq_status lq_set_stream(lq_ctx* ctx, void* cuda_stream);
  *                       LQ_ERR_TIMEOUT path (tests of the failure detection only). */
 enum { LQ_OPT_CUDA_GRAPHS = 1, LQ_OPT_DF64_UPDATES = 2, LQ_OPT_PAIR_SITES = 3, LQ_OPT_STAGED = 4,
        LQ_OPT_BATCH_RHS_PER_THREAD = 5, LQ_OPT_BATCH_PERSISTENT = 6, LQ_OPT_BATCH_BARRIER_TEST = 7,
-       LQ_OPT_BATCH_DEVICE_LOOP = 8, LQ_OPT_HOST_DIRECT = 9, LQ_OPT_BATCH_TILE_ORDER = 10 };
+       LQ_OPT_BATCH_DEVICE_LOOP = 8, LQ_OPT_HOST_DIRECT = 9, LQ_OPT_BATCH_TILE_ORDER = 10,
+       LQ_OPT_DF64_PREFETCH = 11 };
 lq_status lq_set_option(lq_ctx* ctx, int option, int value);
 
 /* Number of lattice sites V. */

@@ -681,6 +681,7 @@ lq_status lq_set_option(lq_ctx* c, int option, int value) {
     case LQ_OPT_BATCH_PERSISTENT: c->batch_persistent = value ? 1 : 0; return LQ_OK;
     case LQ_OPT_BATCH_DEVICE_LOOP: c->batch_device_loop = value ? 1 : 0; return LQ_OK;
     case LQ_OPT_HOST_DIRECT: c->host_direct = value ? 1 : 0; return LQ_OK;
+    case LQ_OPT_DF64_PREFETCH: c->df_prefetch = value ? 1 : 0; return LQ_OK;
     case LQ_OPT_BATCH_TILE_ORDER:
       if (value < 0 || value > 2) return fail(c, LQ_ERR_ARG, "tile order is 0 (tuned), 1 or 2");
       c->batch_order = value;
@@ -754,7 +755,8 @@ lq_status lq_apply_M(lq_ctx* c, double* out, const double* in, double kappa, int
   LQ_TRY(stage_spinor_in(c, in, &din));
   launch_pack_spinor(c->geo, din, s, fin.ref(), c->stream);
   const void* gauge = prec == LQ_F64 ? c->gauge64 : c->gauge_lo[prec];
-  apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites, c->staged);
+  apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites, c->staged,
+               c->df_prefetch);
   LQ_CUDA(c, cudaGetLastError());
   return deliver_spinor(c, fout, out);
 }
@@ -775,8 +777,10 @@ lq_status lq_apply_MdagM(lq_ctx* c, double* out, const double* in, double kappa,
   LQ_TRY(stage_spinor_in(c, in, &din));
   launch_pack_spinor(c->geo, din, s, fin.ref(), c->stream);
   const void* gauge = prec == LQ_F64 ? c->gauge64 : c->gauge_lo[prec];
-  apply_M_prec(c->geo, prec, gauge, fin.ref(), fmid.ref(), kappa, false, c->stream, c->pair_sites, c->staged);
-  apply_M_prec(c->geo, prec, gauge, fmid.ref(), fout.ref(), kappa, true, c->stream, c->pair_sites, c->staged);
+  apply_M_prec(c->geo, prec, gauge, fin.ref(), fmid.ref(), kappa, false, c->stream, c->pair_sites, c->staged,
+               c->df_prefetch);
+  apply_M_prec(c->geo, prec, gauge, fmid.ref(), fout.ref(), kappa, true, c->stream, c->pair_sites, c->staged,
+               c->df_prefetch);
   LQ_CUDA(c, cudaGetLastError());
   return deliver_spinor(c, fout, out);
 }
@@ -851,14 +855,16 @@ lq_status lq_time_dslash(lq_ctx* c, const double* in, double kappa, int dagger, 
   cudaEvent_t e0, e1;
   LQ_CUDA(c, cudaEventCreate(&e0));
   LQ_CUDA(c, cudaEventCreate(&e1));
-  apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites, c->staged);   // warm-up
+  apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites, c->staged,
+               c->df_prefetch);   // warm-up
   double total = 0.0;
   lq_status st = LQ_OK;
   if (flush_l2) {
     for (int i = 0; i < n && st == LQ_OK; ++i) {
       cudaMemsetAsync(flush, i & 0xff, flush_bytes, c->stream);
       cudaEventRecord(e0, c->stream);
-      apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites, c->staged);
+      apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites, c->staged,
+               c->df_prefetch);
       cudaEventRecord(e1, c->stream);
       st = cuda_check(c, cudaEventSynchronize(e1), "cudaEventSynchronize");
       float t = 0.f;
@@ -868,7 +874,8 @@ lq_status lq_time_dslash(lq_ctx* c, const double* in, double kappa, int dagger, 
   } else {
     cudaEventRecord(e0, c->stream);
     for (int i = 0; i < n; ++i)
-      apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites, c->staged);
+      apply_M_prec(c->geo, prec, gauge, fin.ref(), fout.ref(), kappa, dagger != 0, c->stream, c->pair_sites, c->staged,
+               c->df_prefetch);
     cudaEventRecord(e1, c->stream);
     st = cuda_check(c, cudaEventSynchronize(e1), "cudaEventSynchronize");
     float t = 0.f;

@@ -23,7 +23,7 @@ static void apply_one(const Geom& g, const void* gauge, SpinorRef in, SpinorRef 
 }
 
 void apply_M_prec(const Geom& g, int prec, const void* gauge, SpinorRef in, SpinorRef out, double kappa,
-                  bool dagger, cudaStream_t stream, bool pair, bool staged) {
+                  bool dagger, cudaStream_t stream, bool pair, bool staged, bool df_prefetch) {
   if (pair && prec == LQ_I16_12 && pair_geometry(g)) {
     pair_apply(g, gauge, in, out, kappa, dagger, stream);
     return;
@@ -38,8 +38,8 @@ void apply_M_prec(const Geom& g, int prec, const void* gauge, SpinorRef in, Spin
       // the two-threads-per-site double-float operator (lq_dfsplit.cuh)
       DFEpiStore epi{out};
       ReduceScratch none{nullptr, nullptr, 0};
-      if (dagger) launch_dslash_dfsplit<true>(g, gauge, in, kappa, epi, none, stream);
-      else launch_dslash_dfsplit<false>(g, gauge, in, kappa, epi, none, stream);
+      if (dagger) launch_dslash_dfsplit<true>(g, gauge, in, kappa, epi, none, stream, -1, 0, df_prefetch);
+      else launch_dslash_dfsplit<false>(g, gauge, in, kappa, epi, none, stream, -1, 0, df_prefetch);
       break;
     }
     case LQ_I16_12: apply_one<float, GStore::I16_12, SStore::I16>(g, gauge, in, out, kappa, dagger, stream, staged); break;

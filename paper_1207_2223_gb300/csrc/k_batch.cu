@@ -755,6 +755,7 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
     dfa.br = w->br;
     for (int k = 0; k < n; ++k) dfa.gauge_df[k] = ctxs[k]->gauge_lo[LQ_DF64];
     dfa.flat_grid = flat_grid(w);
+    dfa.prefetch = c->df_prefetch != 0;
   }
 
   const int chunk = reliable_every;

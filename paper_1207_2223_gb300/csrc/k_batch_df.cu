@@ -58,10 +58,10 @@ void tail(const BatchDfArgs& a, const BatchDesc& bd, cudaStream_t st) {
     for (int r = 0; r < sd.R; ++r) {
       const int off = sd.off + r * sd.geo.V;
       launch_dslash_dfsplit<false>(sd.geo, a.gauge_df[k], a.xdf, sd.kappa, DFEpiStore{a.tmpdf}, rs, st, bd.total,
-                                   off);
+                                   off, a.prefetch);
       DFEpiResidual<S, DFFinBatch, false> e1{a.phidf, SpinorRef{nullptr, nullptr}, a.rlo,
                                              DFFinBatch{a.st, sd.col + r}};
-      launch_dslash_dfsplit<true>(sd.geo, a.gauge_df[k], a.tmpdf, sd.kappa, e1, rs, st, bd.total, off);
+      launch_dslash_dfsplit<true>(sd.geo, a.gauge_df[k], a.tmpdf, sd.kappa, e1, rs, st, bd.total, off, a.prefetch);
     }
   }
 }

@@ -50,9 +50,11 @@ static void ru(lq_ctx* c, double kappa, cudaStream_t stream) {
   const int k = (int)SLO;
   accumulate_df_kernel<SLO><<<grid_for(g.V, kBS), kBS, 0, stream>>>(g.V, c->x_lo[k].ref(), c->x_df.ref());
   DFEpiStore e0{c->tmp_df.ref()};
-  launch_dslash_dfsplit<false>(g, c->gauge_lo[LQ_DF64], c->x_df.ref(), kappa, e0, c->rs, stream);
+  launch_dslash_dfsplit<false>(g, c->gauge_lo[LQ_DF64], c->x_df.ref(), kappa, e0, c->rs, stream, -1, 0,
+                               c->df_prefetch);
   DFEpiResidual<SLO> e1{c->phi_df.ref(), c->r_df.ref(), c->r_lo[k].ref(), DFFinSolver{c->state}};
-  launch_dslash_dfsplit<true>(g, c->gauge_lo[LQ_DF64], c->tmp_df.ref(), kappa, e1, c->rs, stream);
+  launch_dslash_dfsplit<true>(g, c->gauge_lo[LQ_DF64], c->tmp_df.ref(), kappa, e1, c->rs, stream, -1, 0,
+                              c->df_prefetch);
 }
 
 template <SStore SLO>

@@ -762,6 +762,7 @@ struct BatchDfArgs {
   const void* gauge_df[kMaxSys];   // per system: links as double-float pairs
   int flat_grid;
   bool accumulate, residual;       // which of the two steps to launch
+  bool prefetch;                   // the double-float operator's prefetching variant
 };
 void batch_df_tail(const BatchDfArgs& a, const BatchDesc& bd, SStore s, cudaStream_t st);
 

@@ -118,6 +118,7 @@ struct lq_ctx {
   int batch_device_loop = 1;             // batched solves: the whole solve as one graph with conditional nodes
   int batch_order = 0;                   // batched solves: tile order (0 tuned, 1 site-major, 2 group-major)
   int host_direct = 1;                   // kernels read / write mapped page-locked host buffers in place
+  int df_prefetch = 0;                   // double-float operator: next hop's operands prefetched to shared memory
 };
 
 namespace lq {
@@ -163,7 +164,8 @@ void launch_inner_restart(const Geom& g, SpinorRef src64, SStore s, SpinorRef x,
 // (staged: the stencil that shares x and y links inside a block through shared memory,
 // FP32-arithmetic formats)
 void apply_M_prec(const Geom& g, int prec, const void* gauge, SpinorRef in, SpinorRef out, double kappa,
-                  bool dagger, cudaStream_t stream, bool pair = false, bool staged = false);
+                  bool dagger, cudaStream_t stream, bool pair = false, bool staged = false,
+                  bool df_prefetch = false);
 
 // ---- two-site packed stencil for 16-bit fixed-point storage (k_pair.cu);
 // it pairs x with x + L_t/2 in time, so it needs an even L_t

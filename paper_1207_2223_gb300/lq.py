@@ -174,6 +174,7 @@ LQ_OPT_BATCH_RHS_PER_THREAD, LQ_OPT_BATCH_PERSISTENT, LQ_OPT_BATCH_BARRIER_TEST 
 LQ_OPT_BATCH_DEVICE_LOOP = 8
 LQ_OPT_HOST_DIRECT = 9
 LQ_OPT_BATCH_TILE_ORDER = 10
+LQ_OPT_DF64_PREFETCH = 11
 
 
 def lq_set_option(ctx, option, value):

@@ -152,6 +152,41 @@ def test_page_locked_host_buffers_in_place(lq, dims):
     assert np.array_equal(res[1][2], U)
 
 
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (3, 5, 2, 7), (2, 2, 2, 2), (8, 8, 8, 16)])
+def test_double_float_prefetch_variant_is_identical(lq, dims):
+    """The double-float operator that prefetches the next hop's operands into shared memory
+    (LQ_OPT_DF64_PREFETCH) computes the same arithmetic in the same order: M and M^dag equal the
+    plain variant bit for bit (and the FP64 oracle within 1e-12), and so do a mixed solve with
+    double-float reliable updates and a batched solve of two right-hand sides."""
+    lat, U, psi = _setup(dims, seed=6)
+    res = {}
+    for pf in (0, 1):
+        ctx = lq.lq_create(dims)
+        try:
+            lq.lq_set_option(ctx, lq.LQ_OPT_DF64_PREFETCH, pf)
+            lq.lq_gauge_set(ctx, dev(U))
+            outs = []
+            for d in (False, True):
+                out = torch.empty_like(dev(psi))
+                lq.lq_apply_M(ctx, out, dev(psi), 0.15, d, lq.LQ_DF64)
+                outs.append(host(out))
+            x = torch.zeros_like(dev(psi))
+            status, st = lq.lq_solve_MdagM(ctx, x, dev(psi), 0.15, 1e-10, 5000, lq.LQ_F16_12, 25)
+            assert status == lq.LQ_OK
+            phis = dev(np.stack([psi, source(lat, 6, 1)]))
+            xb = torch.zeros_like(phis)
+            bstatus, bst, _, bres, _ = lq.lq_solve_batch([ctx], [xb], [phis], [0.15], 2, 1e-10, 5000,
+                                                         lq.LQ_F16_12, 25)
+            assert bstatus == lq.LQ_OK and np.all(bres <= 1e-10)
+            res[pf] = outs + [host(x), host(xb)]
+        finally:
+            lq.lq_destroy(ctx)
+    for d, k in ((False, 0), (True, 1)):
+        assert rel_err(res[1][k], o_apply_M(U, psi, dims, 0.15, dagger=d)) < 1e-12
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a, b)
+
+
 def test_free_field_plane_wave(lq):
     """U = 1: the GPU operator reproduces the closed form on a plane wave."""
     dims = (4, 6, 2, 8)
