@@ -52,3 +52,31 @@ def test_create_rejects_bad_shape_without_gpu(lib):
         dims = (ctypes.c_int * 4)(*bad)
         assert lib.lq_create(ctypes.byref(out), dims, 1, None) == 2, bad
         assert not out.value
+
+
+def declared_constants():
+    """Every `NAME = value` of the header's enums (options, precisions, status codes)."""
+    txt = open(os.path.join(ROOT, "include", "lq.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for body in re.findall(r"enum\s*\{([^}]*)\}", txt):
+        nxt = 0
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            m = re.match(r"(LQ_\w+)\s*(?:=\s*(-?\d+))?$", item)
+            assert m, item
+            nxt = int(m.group(2)) if m.group(2) is not None else nxt
+            out[m.group(1)] = nxt
+            nxt += 1
+    return out
+
+
+def test_binding_constants_match_the_header():
+    """The binding's precision, status and option constants equal the header's enums."""
+    from paper_1207_2223_gb300 import lq
+    consts = declared_constants()
+    assert "LQ_OPT_HOST_DIRECT" in consts and "LQ_F16_12" in consts and "LQ_ERR_TIMEOUT" in consts
+    for name, value in consts.items():
+        assert getattr(lq, name) == value, name
