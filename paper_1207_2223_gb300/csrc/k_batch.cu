@@ -376,9 +376,10 @@ Geom flat_geom(int total) {
 // The whole solve as one CUDA graph: a while node over update cycles whose body holds a
 // while node over CG iterations (until a reliable update is due), then the update, with if
 // nodes around the double-float residual and the FP64 certification.  One-thread kernels
-// read the state, take each decision and set the node's condition; every loop counts its
-// bodies against a cap taken from the iteration limit, so the graph ends even if the state
-// never halts.
+// read the state, take each decision and set the node's condition (the iteration loop's
+// condition is set by the first thread of each iteration's last kernel, batch_xpay_kernel);
+// every loop counts its bodies against a cap taken from the iteration limit, so the graph
+// ends even if the state never halts.
 
 // entering the iteration loop: run it unless a reliable update is already due
 __global__ void cond_enter_kernel(BatchState* st, cudaGraphConditionalHandle inner) {
