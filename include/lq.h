@@ -264,8 +264,9 @@ lq_status lq_solve_MdagM(lq_ctx* ctx, double* x, const double* phi, double kappa
  *            of every column per iteration
  *   iters    optional host int[n * nrhs]: iterations until each column was frozen
  *   resid    optional host double[n * nrhs]: final FP64 true relative residuals
- * Synchronises.  Errors: LQ_ERR_ARG (host buffers, sizes), LQ_ERR_STATE,
- * LQ_ERR_NOT_CONVERGED, LQ_ERR_NAN, LQ_ERR_CUDA (message on ctxs[0]). */
+ * Synchronises.  Errors: LQ_ERR_ARG (host buffers, sizes), LQ_ERR_SHAPE (more than 2^30
+ * sites x right-hand sides in all), LQ_ERR_STATE, LQ_ERR_NOT_CONVERGED, LQ_ERR_NAN,
+ * LQ_ERR_TIMEOUT (persistent launch), LQ_ERR_CUDA (message on ctxs[0]). */
 lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const double** phi, const double* kappa, int nrhs,
                          double tol, int maxiter, int inner_prec, int reliable_every, double* hist, int hist_len,
                          int* iters, double* resid, lq_solve_stats* stats);

@@ -38,6 +38,7 @@
 // or every open column's iterated residual has met the tolerance, x is
 // certified with the FP64 operator, which reopens any column that fails.
 #include <algorithm>
+#include <climits>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -577,6 +578,12 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
         return fail(LQ_ERR_ARG, "x and phi must be device buffers");
       }
     }
+  }
+  {
+    // element indices of the batch fields are 32-bit (with room for a grid stride)
+    long long elements = 0;
+    for (int k = 0; k < n; ++k) elements += (long long)ctxs[k]->geo.V * nrhs;
+    if (elements > (long long)(INT_MAX / 2)) return fail(LQ_ERR_SHAPE, "batch too large for 32-bit element indices");
   }
   cudaStream_t st = c->stream;
   const bool dfru = c->df_updates != 0;      // double-float intermediate reliable updates
