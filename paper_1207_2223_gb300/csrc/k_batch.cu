@@ -209,7 +209,7 @@ struct BatchWork {
   struct Recorded {
     BatchDesc bd;
     int form;                     // kFormChunk, kFormLoop64, kFormLoopDF
-    int chunk;                    // iterations of a chunk graph
+    int chunk;                    // iterations of a chunk graph; operator variant of a loop graph
     cudaGraphExec_t exec;
   };
   std::vector<Recorded> graphs;
@@ -773,11 +773,13 @@ extern "C" lq_status lq_solve_batch(lq_ctx** ctxs, int n, double** x, const doub
   if (!host_loop) {
     // the whole solve as one graph with conditional nodes; a launch that its loop caps
     // ended early is repeated (at most a few times)
+    // the graph bakes in the double-float operator variant: part of its key
     const int form = dfru ? kFormLoopDF : kFormLoop64;
-    cudaGraphExec_t exec = find_graph(w, bd, form, 0);
+    const int variant = dfru && dfa.prefetch ? 1 : 0;
+    cudaGraphExec_t exec = find_graph(w, bd, form, variant);
     if (!exec) {
       err = build_solve_graph(w, bd, bd64, inner_prec, tu, dfru ? &dfa : nullptr, &exec);
-      if (err == cudaSuccess) keep_graph(w, bd, form, 0, exec);
+      if (err == cudaSuccess) keep_graph(w, bd, form, variant, exec);
     }
     for (int launch = 0; launch < 4 && err == cudaSuccess; ++launch) {
       err = cudaGraphLaunch(exec, st);
